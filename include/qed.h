@@ -1,0 +1,217 @@
+/*
+ * qed.h — C ABI of libqed, a single-GPU (GB300, sm_103a) integrator of the quantum
+ * master equation (QME) of finite-dimensional cavity QED models.
+ *
+ * The method (Li, Miao, Ozhigov, "Supercomputer model of finite-dimensional quantum
+ * electrodynamics applications"):
+ *   - Sec. 2, first point: basis states are strings of digits (photon numbers of the
+ *     cavity modes, atom bits, further two-level degrees of freedom); H is the energy
+ *     operator on that basis (Eqs. 6-12 give the JC/TC/JCH terms used here).
+ *   - Sec. 2, second point: the QME i hbar rho' = [H, rho] + i L(rho) (Eq. 2) with the
+ *     Lindblad term L(rho) = sum_j gamma_j (A_j rho A_j^+ - 1/2 {A_j^+ A_j, rho}) (Eq. 3).
+ *   - Sec. 4.2, Table 3: the two stages "Taylor approximation" (the propagator
+ *     U = exp(-i H dt), here by scaling-and-squaring Pade in FP64 on the GPU) and
+ *     "unitary evolution" (rho -> U rho U^+ per step, followed here by one explicit
+ *     Euler step of the Lindblad term).
+ *
+ * Units: hbar = 1; every frequency, coupling and rate is an angular frequency.
+ *
+ * Memory: every rho / records / gradient buffer is owned by the caller (device memory
+ * unless stated otherwise).  Operators, propagators and work space are owned by the
+ * model and released by qed_free.  All device work is enqueued on the caller's stream;
+ * only qed_build and qed_sync_status synchronise.  Errors are returned as codes (never
+ * abort/exit/trap); qed_last_error() gives a thread-local message for the last failure.
+ *
+ * Density matrices are complex128, row-major, D x D, interleaved (re, im) — the layout
+ * of a contiguous torch.complex128 tensor.  Rows and columns follow the basis order
+ * returned by qed_basis_labels.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st *qed_stream;
+
+typedef enum {
+    QED_OK = 0,
+    QED_EINVAL = 1,        /* bad argument or model specification              */
+    QED_ENOMEM = 2,        /* device or host allocation failed                 */
+    QED_ECUDA = 3,         /* a CUDA runtime/driver call failed                */
+    QED_ETIMEOUT = 4,      /* a bounded device wait ran out                    */
+    QED_ENUMERIC = 5,      /* non-finite values or a singular Pade denominator */
+    QED_EUNSUPPORTED = 6   /* valid request this build does not implement      */
+} qed_status;
+
+typedef enum {
+    QED_FP64 = 0,          /* U rho U^+ as two FP64 complex GEMMs                          */
+    QED_SPLIT_FP16x2 = 1,  /* increment form on tcgen05: FP16 hi+lo operands, FP32 accumulate */
+    QED_SPLIT_BF16x3 = 2,  /* reserved                                                    */
+    QED_SPLIT_TF32x3 = 3   /* reserved                                                    */
+} qed_precision;
+
+/* Basis kinds (Sec. 4.2, Eqs. 10-11 restrict the 2^Area product space to one photon). */
+enum {
+    QED_BASIS_FULL = 0,        /* full product space, mixed-radix order (first digit slowest) */
+    QED_BASIS_CAP = 1,         /* states with <= excitation_cap excitations, mixed-radix order */
+    QED_BASIS_SINGLE_G = 2,    /* vacuum, then per cavity: its photon, then its atoms          */
+    QED_BASIS_FIRST_D = 3,     /* first dim_cap states ordered by (excitations, mixed radix)  */
+    QED_BASIS_SECTOR = 4       /* exactly excitation_cap excitations, mixed-radix order       */
+};
+
+/* Jump operator kinds for Eq. (3). */
+enum {
+    QED_JUMP_A = 0,        /* a_c: photon loss from cavity `site`                               */
+    QED_JUMP_SIGMA = 1,    /* sigma_a: decay of atom `site` (atoms numbered cavity by cavity)   */
+    QED_JUMP_DEPHASE = 2,  /* sigma_z = |1><1| - |0><0| on extra two-level digit `site`         */
+    QED_JUMP_LEAK = 3      /* |G><photon_c|: the one-photon state of cavity `site` -> vacuum    */
+};
+
+/*
+ * Model specification (Sec. 2, first two points).  Digits of a basis state: for each
+ * cavity c its photon number 0..n_max[c] followed by one bit per atom in that cavity,
+ * then one bit per extra two-level degree of freedom.  An excitation is a photon or an
+ * excited atom (extra digits are not counted).
+ *
+ * H = sum_c omega_c a_c^+ a_c + sum_a omega_a s_a^+ s_a            (Eqs. 8b-8d, 12)
+ *   + sum_a g[a] (a_c(a)^+ s_a + a_c(a) s_a^+)                     (JC / TC coupling, Eq. 8b)
+ *   + sum_b zeta[b] (a_i^+ a_j + a_i a_j^+),  (i, j) = bond_ij[2b..2b+1]   (hopping, Eq. 12)
+ *   + sum_x extra_tunnel[x] sigma_x(x)                              (two-site tunnelling, Eq. 4)
+ * projected on the chosen basis.  All arrays are caller-owned and copied by the callee.
+ */
+typedef struct {
+    int32_t n_cavities;
+    const int32_t *atoms_per_cavity;   /* [n_cavities] */
+    const int32_t *n_max;              /* [n_cavities] photon truncation */
+    int32_t n_extra;
+    int32_t basis_kind;                /* QED_BASIS_* */
+    int32_t excitation_cap;
+    int64_t dim_cap;
+    double omega_c, omega_a;
+    const double *g;                   /* [total atoms] */
+    int32_t n_bonds;
+    const int32_t *bond_ij;            /* [2 * n_bonds] cavity pairs */
+    const double *zeta;                /* [n_bonds] */
+    const double *extra_tunnel;        /* [n_extra] */
+    int32_t n_jumps;
+    const int32_t *jump_kind;          /* [n_jumps] QED_JUMP_* */
+    const int32_t *jump_site;          /* [n_jumps] */
+    const double *gamma;               /* [n_jumps] rates, >= 0 */
+} qed_spec;
+
+typedef struct qed_model qed_model;   /* opaque, library-owned */
+
+/* ---------------------------------------------------------------- host-only queries
+ * These run the host-side model builder only (no GPU needed).                         */
+
+/* Basis dimension and digit count of a specification.  EINVAL on a malformed spec. */
+qed_status qed_spec_dim(const qed_spec *spec, int64_t *dim, int32_t *n_digits);
+
+/* Basis states as digits, host int32 [dim x n_digits] (capacity in elements). */
+qed_status qed_spec_basis(const qed_spec *spec, int32_t *digits, int64_t capacity);
+
+/* Dense projected H, host complex128 [dim x dim] interleaved (capacity in complex). */
+qed_status qed_spec_hamiltonian(const qed_spec *spec, double *H, int64_t capacity);
+
+/* Dense projected A_j (not scaled by gamma), host complex128 [dim x dim]. */
+qed_status qed_spec_jump(const qed_spec *spec, int32_t j, double *A, int64_t capacity);
+
+/* ---------------------------------------------------------------- model lifetime */
+
+/* Build basis, H, jump tables and observables on the host, upload them, and compute
+ * U = exp(-i H dt) on the device in FP64 (Pade-13 scaling and squaring; the
+ * "Taylor approximation" stage of Sec. 4.2).  In split precision also prepares the
+ * diagonal phase P = diag(exp(-i H_kk dt)), Delta = P^-1 U - I and its FP16 hi/lo
+ * operand planes.  Synchronises `stream`.  EINVAL on a bad spec, ENOMEM, ECUDA,
+ * ENUMERIC (singular Pade denominator), EUNSUPPORTED for reserved precisions. */
+qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_stream stream,
+                     qed_model **out);
+
+qed_status qed_free(qed_model *m);
+
+qed_status qed_dim(const qed_model *m, int64_t *dim);
+
+/* Digits of every basis state, host int32 [dim x n_digits]; n_digits from qed_spec_dim. */
+qed_status qed_basis_labels(const qed_model *m, int32_t *digits);
+
+/* Index of the basis state with the given digits (host int32 [n_digits]); EINVAL and
+ * *index = -1 if it is not in the basis. */
+qed_status qed_basis_index(const qed_model *m, const int32_t *digits, int64_t *index);
+
+/* Number of observable ids: ids 0..dim-1 are populations rho_kk; id dim is the trace;
+ * then <n_c> per cavity, <s_a^+ s_a> per atom, and the extra digits' <1|.|1>. */
+qed_status qed_n_observables(const qed_model *m, int32_t *n);
+
+/* Steps between trace renormalisation + Hermitian symmetrisation in split precision
+ * (0 = never; default 100).  Ignored in FP64. */
+qed_status qed_set_renorm_every(qed_model *m, int32_t every);
+
+/* ---------------------------------------------------------------- hot path */
+
+/*
+ * Advance rho (device complex128 D x D, in/out) by n_steps steps of
+ *     V = U rho U^+                          ("unitary evolution", Sec. 4.2, Eq. 2)
+ *     rho <- V + dt sum_j gamma_j (A_j V A_j^+ - 1/2 {A_j^+ A_j, V})      (Eq. 3)
+ * Records observables obs_ids (host int32 [n_obs]) into records (device FP64,
+ * row-major [n_rec x n_obs]) at every local step i in 0..n_steps (before step i+1)
+ * with (step_offset + i) % record_every == 0; records may be NULL when n_obs == 0.
+ * n_rec = number of such i.  Asynchronous on `stream`: device-side errors (non-finite
+ * trace at a renormalisation) surface through qed_sync_status.
+ */
+qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_offset,
+                      int32_t record_every, int32_t n_obs, const int32_t *obs_ids,
+                      double *records, qed_stream stream);
+
+/* Observables of one rho (device) into out (device FP64 [n_obs]). */
+qed_status qed_observables(const qed_model *m, const void *rho, int32_t n_obs,
+                           const int32_t *obs_ids, double *out, qed_stream stream);
+
+/* Synchronise `stream` and report device-side errors raised since the last call. */
+qed_status qed_sync_status(qed_model *m, qed_stream stream);
+
+/* ---------------------------------------------------------------- test and measurement hooks */
+
+/* Replace U by a caller-provided propagator (device complex128 D x D), e.g. the
+ * oracle's, so the step can be compared without the expm's own rounding.  Recomputes
+ * Delta and its planes in split precision.  Synchronises `stream`. */
+qed_status qed_set_U(qed_model *m, const void *U, qed_stream stream);
+
+/* Copy the model's U (device complex128 D x D) into caller memory (device). */
+qed_status qed_get_U(const qed_model *m, void *U, qed_stream stream);
+
+/*
+ * Run n_steps steps like qed_evolve (no records), timing each kernel class with CUDA
+ * events on `stream`; writes the mean duration in milliseconds per step of each class
+ * into ms[0..n_kernels-1] and the class names (comma separated) into names (size
+ * name_cap).  Synchronises.  For measurement only: it perturbs the pipelining.
+ */
+qed_status qed_profile(qed_model *m, void *rho, int64_t n_steps, double *ms, int32_t n_kernels,
+                       char *names, int32_t name_cap, qed_stream stream);
+
+/*
+ * The tensor-core product of the split-precision step, exposed for testing:
+ *     out[s] = sum over the K-slices of slice s of (A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T)
+ * with A = a_planes (device FP16 [2][M][K], hi plane then lo plane, K contiguous) and
+ * B = b_planes (device FP16 [2][N][K]); out is device FP32 [splits][M][N] (split-K partial
+ * sums; their sum is the product).  M and N multiples of 128, K of 64, planes 16-byte
+ * aligned.  tcgen05.mma (kind::f16, FP32 accumulation in tensor memory) fed by TMA.
+ * Synchronises `stream`.  EINVAL on bad shapes, ETIMEOUT if a bounded wait ran out.
+ */
+qed_status qed_tc_gemm(const void *a_planes, const void *b_planes, int32_t M, int32_t N, int32_t K,
+                       int32_t splits, float *out, qed_stream stream);
+
+/* Total number of kernels this library has launched in this process (all models). */
+qed_status qed_launch_count(int64_t *count);
+
+const char *qed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QED_H */

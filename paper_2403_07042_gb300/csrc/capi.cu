@@ -1,0 +1,482 @@
+// The C ABI of libqed (declared in include/qed.h): argument checks, model lifetime,
+// the propagator stage and the step loop.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "model.h"
+#include "split.h"
+
+namespace qed {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+qed_status einval(const std::string &msg) {
+    set_error(msg);
+    return QED_EINVAL;
+}
+
+template <class T>
+qed_status dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? QED_ENOMEM : QED_ECUDA;
+    }
+    return QED_OK;
+}
+
+#define QED_TRY(expr)                       \
+    do {                                    \
+        qed_status st_ = (expr);            \
+        if (st_ != QED_OK) return st_;      \
+    } while (0)
+
+// Pade-13 coefficients b_j = (2m-j)! m! / ((2m)! j! (m-j)!), m = 13, scaled so b_13 = 1
+// (Higham, SIAM J. Matrix Anal. Appl. 26(4), 2005): b_j = (26-j)! / (j! (13-j)!).
+void pade13_coefficients(double b[14]) {
+    for (int j = 0; j <= 13; ++j) {
+        long double v = 1.0L;
+        for (int q = 14 - j; q <= 26 - j; ++q) v *= q;  // (26-j)! / (13-j)!
+        for (int q = 2; q <= j; ++q) v /= q;            // / j!
+        b[j] = (double)v;
+    }
+}
+
+// theta_13 of the Pade-13 scaling-and-squaring method (Higham 2005, Table 2.3): the
+// largest 1-norm of X for which the degree-13 approximant is accurate to unit roundoff.
+constexpr double kTheta13 = 5.371920351148152;
+
+// U = exp(X) with X = -i dt H (H device, D x D).  Allocates its own work space.
+qed_status propagator(cudaStream_t s, int64_t D, double dt, const double2 *H, double h_norm1, double2 *U,
+                      uint32_t *err) {
+    double b[14];
+    pade13_coefficients(b);
+    const double xnorm = dt * h_norm1;
+    int sq = 0;
+    if (xnorm > kTheta13) sq = (int)std::ceil(std::log2(xnorm / kTheta13));
+    const double theta = std::ldexp(dt, -sq);
+    const size_t DD = (size_t)(D * D);
+    double2 *buf = nullptr;
+    QED_TRY(dev_alloc(&buf, DD * 9));
+    double2 *X = buf, *X2 = buf + DD, *X4 = buf + 2 * DD, *X6 = buf + 3 * DD, *T = buf + 4 * DD,
+            *Up = buf + 5 * DD, *Vp = buf + 6 * DD, *aug = buf + 7 * DD;  // aug takes 2 DD
+    scale_minus_i(s, D, theta, H, X);
+    zgemm(s, D, D, D, 1.0, X, D, X, D, false, 0.0, X2, D);
+    zgemm(s, D, D, D, 1.0, X2, D, X2, D, false, 0.0, X4, D);
+    zgemm(s, D, D, D, 1.0, X4, D, X2, D, false, 0.0, X6, D);
+    // U_p = X [X6 (b13 X6 + b11 X4 + b9 X2) + b7 X6 + b5 X4 + b3 X2 + b1 I]
+    zlincomb(s, D, b[13], X6, b[11], X4, b[9], X2, 0.0, 0.0, T);
+    zgemm(s, D, D, D, 1.0, X6, D, T, D, false, 0.0, Vp, D);
+    zlincomb(s, D, b[7], X6, b[5], X4, b[3], X2, b[1], 1.0, Vp);
+    zgemm(s, D, D, D, 1.0, X, D, Vp, D, false, 0.0, Up, D);
+    // V_p = X6 (b12 X6 + b10 X4 + b8 X2) + b6 X6 + b4 X4 + b2 X2 + b0 I
+    zlincomb(s, D, b[12], X6, b[10], X4, b[8], X2, 0.0, 0.0, T);
+    zgemm(s, D, D, D, 1.0, X6, D, T, D, false, 0.0, Vp, D);
+    zlincomb(s, D, b[6], X6, b[4], X4, b[2], X2, b[0], 1.0, Vp);
+    // solve (V_p - U_p) R = V_p + U_p
+    pade_augment(s, D, Up, Vp, aug);
+    gauss_jordan(s, D, aug, err);
+    take_right_half(s, D, aug, U);
+    // undo the scaling: R^(2^sq)
+    for (int q = 0; q < sq; ++q) {
+        zgemm(s, D, D, D, 1.0, U, D, U, D, false, 0.0, T, D);
+        cudaMemcpyAsync(U, T, DD * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_error(std::string("propagator: ") + cudaGetErrorString(e));
+        return QED_ECUDA;
+    }
+    return QED_OK;
+}
+
+void release(qed_model *m) {
+    if (!m) return;
+    void *ptrs[] = {m->U, m->work1, m->work2, m->phase, m->anti, m->in_ptr, m->in_jump, m->in_src,
+                    m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (m->err_host) cudaFreeHost(m->err_host);
+    split_release(m);
+    for (auto &e : m->ev)
+        if (e) cudaEventDestroy(e);
+    delete m;
+}
+
+qed_status upload_tables(qed_model *m) {
+    const HostModel &hm = m->host;
+    const int64_t D = m->D;
+    // incoming jump lists, grouped by destination row and sorted by jump id
+    std::vector<std::vector<JumpEntry>> rows((size_t)D);
+    for (const auto &e : hm.jumps) rows[(size_t)e.dst].push_back(e);
+    std::vector<int32_t> ptr((size_t)D + 1, 0), jump, src;
+    std::vector<double> coef;
+    int32_t max_in = 0;
+    for (int64_t r = 0; r < D; ++r) {
+        auto &v = rows[(size_t)r];
+        std::sort(v.begin(), v.end(), [](const JumpEntry &a, const JumpEntry &b) { return a.jump < b.jump; });
+        for (const auto &e : v) {
+            jump.push_back(e.jump);
+            src.push_back((int32_t)e.src);
+            coef.push_back(e.coef * std::sqrt(hm.gamma[(size_t)e.jump]));
+        }
+        ptr[(size_t)r + 1] = (int32_t)jump.size();
+        max_in = std::max(max_in, (int32_t)v.size());
+    }
+    m->n_in = (int64_t)jump.size();
+    m->max_in = max_in;
+    QED_TRY(dev_alloc(&m->in_ptr, ptr.size()));
+    QED_TRY(dev_alloc(&m->in_jump, jump.size()));
+    QED_TRY(dev_alloc(&m->in_src, src.size()));
+    QED_TRY(dev_alloc(&m->in_coef, coef.size()));
+    QED_CUDA_TRY(cudaMemcpy(m->in_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
+    if (!jump.empty()) {
+        QED_CUDA_TRY(cudaMemcpy(m->in_jump, jump.data(), jump.size() * 4, cudaMemcpyHostToDevice));
+        QED_CUDA_TRY(cudaMemcpy(m->in_src, src.data(), src.size() * 4, cudaMemcpyHostToDevice));
+        QED_CUDA_TRY(cudaMemcpy(m->in_coef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice));
+    }
+    QED_TRY(dev_alloc(&m->anti, (size_t)D));
+    QED_CUDA_TRY(cudaMemcpy(m->anti, hm.anti_diag.data(), (size_t)D * 8, cudaMemcpyHostToDevice));
+    // observables: trace, photons per cavity, atoms, extra digits
+    const Layout &L = hm.layout;
+    const int nd = L.n_digits();
+    std::vector<int> digit_of;
+    for (int p : L.photon_digit) digit_of.push_back(p);
+    for (int p : L.atom_digit) digit_of.push_back(p);
+    for (int p : L.extra_digit) digit_of.push_back(p);
+    m->n_named = 1 + (int32_t)digit_of.size();
+    std::vector<double> w((size_t)m->n_named * (size_t)D, 0.0);
+    for (int64_t k = 0; k < D; ++k) {
+        w[(size_t)k] = 1.0;
+        for (size_t q = 0; q < digit_of.size(); ++q)
+            w[(size_t)(q + 1) * (size_t)D + (size_t)k] = hm.digits[(size_t)k * nd + digit_of[q]];
+    }
+    QED_TRY(dev_alloc(&m->obs_w, w.size()));
+    QED_CUDA_TRY(cudaMemcpy(m->obs_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+    // phases P_k = exp(-i H_kk dt)
+    std::vector<double2> ph((size_t)D);
+    std::vector<double> diag((size_t)D, 0.0);
+    for (const auto &e : hm.h_entries)
+        if (e.row == e.col) diag[(size_t)e.row] += entry_coefficient(hm, e) * e.unit;
+    for (int64_t k = 0; k < D; ++k)
+        ph[(size_t)k] = make_double2(std::cos(diag[(size_t)k] * m->dt), -std::sin(diag[(size_t)k] * m->dt));
+    QED_TRY(dev_alloc(&m->phase, (size_t)D));
+    QED_CUDA_TRY(cudaMemcpy(m->phase, ph.data(), (size_t)D * 16, cudaMemcpyHostToDevice));
+    return QED_OK;
+}
+
+qed_status ensure_ids(qed_model *m, int32_t n_obs, const int32_t *ids, cudaStream_t s) {
+    if (n_obs <= 0) return QED_OK;
+    if (!ids) return einval("obs_ids is NULL");
+    const int32_t lim = (int32_t)m->D + m->n_named;
+    for (int32_t o = 0; o < n_obs; ++o)
+        if (ids[o] < 0 || ids[o] >= lim) return einval("observable id out of range");
+    if (n_obs > m->obs_ids_cap) {
+        if (m->obs_ids_dev) {
+            cudaStreamSynchronize(s);
+            cudaFree(m->obs_ids_dev);
+            m->obs_ids_dev = nullptr;
+        }
+        QED_TRY(dev_alloc(&m->obs_ids_dev, (size_t)n_obs));
+        m->obs_ids_cap = n_obs;
+    }
+    QED_CUDA_TRY(cudaMemcpyAsync(m->obs_ids_dev, ids, (size_t)n_obs * 4, cudaMemcpyHostToDevice, s));
+    return QED_OK;
+}
+
+
+}  // namespace
+
+// One FP64 step: V = (U rho) U^+, then the Lindblad update (Eq. 3) into rho.
+void step_f64(qed_model *m, double2 *rho, cudaStream_t s) {
+    const int64_t D = m->D;
+    zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);
+    zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
+    dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, m->dt);
+}
+
+}  // namespace qed
+
+using namespace qed;
+
+extern "C" {
+
+const char *qed_last_error(void) { return g_last_error.c_str(); }
+
+qed_status qed_launch_count(int64_t *count) {
+    if (!count) return einval("count is NULL");
+    *count = launches();
+    return QED_OK;
+}
+
+qed_status qed_spec_dim(const qed_spec *spec, int64_t *dim, int32_t *n_digits) {
+    if (!dim) return einval("dim is NULL");
+    HostModel hm;
+    std::string err;
+    qed_status st = build_host_model(spec, hm, err, false);
+    if (st != QED_OK) { set_error(err); return st; }
+    *dim = hm.dim;
+    if (n_digits) *n_digits = hm.layout.n_digits();
+    return QED_OK;
+}
+
+qed_status qed_spec_basis(const qed_spec *spec, int32_t *digits, int64_t capacity) {
+    HostModel hm;
+    std::string err;
+    qed_status st = build_host_model(spec, hm, err, false);
+    if (st != QED_OK) { set_error(err); return st; }
+    if (!digits || capacity < (int64_t)hm.digits.size()) return einval("digits buffer too small");
+    for (size_t i = 0; i < hm.digits.size(); ++i) digits[i] = hm.digits[i];
+    return QED_OK;
+}
+
+qed_status qed_spec_hamiltonian(const qed_spec *spec, double *H, int64_t capacity) {
+    HostModel hm;
+    std::string err;
+    qed_status st = build_host_model(spec, hm, err, true);
+    if (st != QED_OK) { set_error(err); return st; }
+    if (!H || capacity < hm.dim * hm.dim) return einval("H buffer too small");
+    std::vector<cplx> Hd;
+    dense_hamiltonian(hm, Hd);
+    std::memcpy(H, Hd.data(), Hd.size() * sizeof(cplx));
+    return QED_OK;
+}
+
+qed_status qed_spec_jump(const qed_spec *spec, int32_t j, double *A, int64_t capacity) {
+    HostModel hm;
+    std::string err;
+    qed_status st = build_host_model(spec, hm, err, true);
+    if (st != QED_OK) { set_error(err); return st; }
+    if (j < 0 || j >= (int32_t)hm.gamma.size()) return einval("jump index out of range");
+    if (!A || capacity < hm.dim * hm.dim) return einval("A buffer too small");
+    std::memset(A, 0, (size_t)(hm.dim * hm.dim) * 16);
+    for (const auto &e : hm.jumps)
+        if (e.jump == j) A[2 * (e.dst * hm.dim + e.src)] += e.coef;
+    return QED_OK;
+}
+
+qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_stream stream, qed_model **out) {
+    if (!out) return einval("out is NULL");
+    *out = nullptr;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return einval("dt must be finite and > 0");
+    if (prec != QED_FP64 && prec != QED_SPLIT_FP16x2) {
+        set_error("precision not implemented in this build");
+        return QED_EUNSUPPORTED;
+    }
+    std::unique_ptr<qed_model, void (*)(qed_model *)> m(new qed_model(), release);
+    std::string err;
+    qed_status st = build_host_model(spec, m->host, err, true);
+    if (st != QED_OK) { set_error(err); return st; }
+    m->D = m->host.dim;
+    m->dt = dt;
+    m->prec = prec;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t D = m->D;
+    const size_t DD = (size_t)(D * D);
+    QED_TRY(dev_alloc(&m->U, DD));
+    QED_TRY(dev_alloc(&m->work1, DD));
+    QED_TRY(dev_alloc(&m->work2, DD));
+    QED_TRY(dev_alloc(&m->scalars, 16));
+    QED_TRY(dev_alloc(&m->err, 1));
+    QED_CUDA_TRY(cudaMallocHost((void **)&m->err_host, sizeof(uint32_t)));
+    *m->err_host = 0;
+    QED_CUDA_TRY(cudaMemset(m->err, 0, sizeof(uint32_t)));
+    QED_TRY(upload_tables(m.get()));
+    for (auto &e : m->ev) QED_CUDA_TRY(cudaEventCreate(&e));
+    // H into work1, then U = exp(-i H dt)
+    std::vector<cplx> Hd;
+    dense_hamiltonian(m->host, Hd);
+    double norm1 = 0.0;
+    for (int64_t c = 0; c < D; ++c) {
+        double col = 0.0;
+        for (int64_t r = 0; r < D; ++r) col += std::abs(Hd[(size_t)(r * D + c)]);
+        norm1 = std::max(norm1, col);
+    }
+    QED_CUDA_TRY(cudaMemcpyAsync(m->work1, Hd.data(), DD * 16, cudaMemcpyHostToDevice, s));
+    QED_TRY(propagator(s, D, dt, m->work1, norm1, m->U, m->err));
+    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
+    if (*m->err_host & kErrSingular) {
+        set_error("singular Pade denominator");
+        return QED_ENUMERIC;
+    }
+    if (prec != QED_FP64) QED_TRY(split_prepare(m.get(), s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = m.release();
+    return QED_OK;
+}
+
+qed_status qed_free(qed_model *m) {
+    if (!m) return einval("model is NULL");
+    cudaDeviceSynchronize();
+    release(m);
+    return QED_OK;
+}
+
+qed_status qed_dim(const qed_model *m, int64_t *dim) {
+    if (!m || !dim) return einval("NULL argument");
+    *dim = m->D;
+    return QED_OK;
+}
+
+qed_status qed_basis_labels(const qed_model *m, int32_t *digits) {
+    if (!m || !digits) return einval("NULL argument");
+    for (size_t i = 0; i < m->host.digits.size(); ++i) digits[i] = m->host.digits[i];
+    return QED_OK;
+}
+
+qed_status qed_basis_index(const qed_model *m, const int32_t *digits, int64_t *index) {
+    if (!m || !digits || !index) return einval("NULL argument");
+    const int nd = m->host.layout.n_digits();
+    std::vector<uint8_t> d((size_t)nd);
+    for (int i = 0; i < nd; ++i) {
+        if (digits[i] < 0 || digits[i] >= m->host.layout.radix[(size_t)i]) {
+            *index = -1;
+            return einval("digit out of range");
+        }
+        d[(size_t)i] = (uint8_t)digits[i];
+    }
+    auto it = m->host.index.find(state_key(d.data(), nd));
+    *index = it == m->host.index.end() ? -1 : it->second;
+    if (*index < 0) return einval("state not in the basis");
+    return QED_OK;
+}
+
+qed_status qed_n_observables(const qed_model *m, int32_t *n) {
+    if (!m || !n) return einval("NULL argument");
+    *n = (int32_t)m->D + m->n_named;
+    return QED_OK;
+}
+
+qed_status qed_set_renorm_every(qed_model *m, int32_t every) {
+    if (!m || every < 0) return einval("bad argument");
+    m->renorm_every = every;
+    return QED_OK;
+}
+
+qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_offset, int32_t record_every,
+                      int32_t n_obs, const int32_t *obs_ids, double *records, qed_stream stream) {
+    if (!m || !rho_v) return einval("NULL model or rho");
+    if (n_steps < 0 || step_offset < 0) return einval("negative step count");
+    if (n_obs < 0) return einval("negative n_obs");
+    if (n_obs > 0 && (record_every <= 0 || !records)) return einval("records need record_every > 0 and a buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    QED_TRY(ensure_ids(m, n_obs, obs_ids, s));
+    double2 *rho = (double2 *)rho_v;
+    int64_t row = 0;
+    if (m->prec != QED_FP64) QED_TRY(split_begin(m, rho, s));
+    for (int64_t i = 0; i <= n_steps; ++i) {
+        if (n_obs > 0 && (step_offset + i) % record_every == 0) {
+            if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
+            observables(s, m->D, rho, m->obs_w, m->obs_ids_dev, n_obs, records + row * n_obs);
+            ++row;
+        }
+        if (i == n_steps) break;
+        if (m->prec == QED_FP64) {
+            step_f64(m, rho, s);
+        } else {
+            split_step(m, rho, s);
+            if (m->renorm_every > 0 && (step_offset + i + 1) % m->renorm_every == 0) split_renorm(m, rho, s);
+        }
+    }
+    if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
+    QED_CUDA_TRY(cudaGetLastError());
+    return QED_OK;
+}
+
+qed_status qed_observables(const qed_model *m_c, const void *rho, int32_t n_obs, const int32_t *obs_ids, double *out,
+                           qed_stream stream) {
+    qed_model *m = const_cast<qed_model *>(m_c);
+    if (!m || !rho || !out) return einval("NULL argument");
+    if (n_obs <= 0) return einval("n_obs must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    QED_TRY(ensure_ids(m, n_obs, obs_ids, s));
+    observables(s, m->D, (const double2 *)rho, m->obs_w, m->obs_ids_dev, n_obs, out);
+    QED_CUDA_TRY(cudaGetLastError());
+    return QED_OK;
+}
+
+qed_status qed_sync_status(qed_model *m, qed_stream stream) {
+    if (!m) return einval("NULL model");
+    cudaStream_t s = (cudaStream_t)stream;
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    QED_CUDA_TRY(cudaGetLastError());
+    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
+    uint32_t e = *m->err_host;
+    QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+    if (e & kErrTimeout) { set_error("a bounded device wait ran out"); return QED_ETIMEOUT; }
+    if (e & kErrNonFinite) { set_error("non-finite or non-positive trace at renormalisation"); return QED_ENUMERIC; }
+    if (e & kErrSingular) { set_error("singular matrix"); return QED_ENUMERIC; }
+    return QED_OK;
+}
+
+qed_status qed_set_U(qed_model *m, const void *U, qed_stream stream) {
+    if (!m || !U) return einval("NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    QED_CUDA_TRY(cudaMemcpyAsync(m->U, U, (size_t)(m->D * m->D) * 16, cudaMemcpyDeviceToDevice, s));
+    if (m->prec != QED_FP64) QED_TRY(split_prepare(m, s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    return QED_OK;
+}
+
+qed_status qed_get_U(const qed_model *m, void *U, qed_stream stream) {
+    if (!m || !U) return einval("NULL argument");
+    QED_CUDA_TRY(cudaMemcpyAsync(U, m->U, (size_t)(m->D * m->D) * 16, cudaMemcpyDeviceToDevice,
+                                 (cudaStream_t)stream));
+    return QED_OK;
+}
+
+qed_status qed_profile(qed_model *m, void *rho_v, int64_t n_steps, double *ms, int32_t n_kernels, char *names,
+                       int32_t name_cap, qed_stream stream) {
+    if (!m || !rho_v || !ms || n_steps <= 0) return einval("bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double2 *rho = (double2 *)rho_v;
+    std::vector<double> acc(8, 0.0);
+    std::string label;
+    int classes = 0;
+    if (m->prec != QED_FP64) QED_TRY(split_begin(m, rho, s));
+    for (int64_t i = 0; i < n_steps; ++i) {
+        if (m->prec == QED_FP64) {
+            const int64_t D = m->D;
+            cudaEventRecord(m->ev[0], s);
+            zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);
+            cudaEventRecord(m->ev[1], s);
+            zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
+            cudaEventRecord(m->ev[2], s);
+            dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, m->dt);
+            cudaEventRecord(m->ev[3], s);
+            classes = 3;
+            label = "zgemm_f64_1,zgemm_f64_2,dissipate_f64";
+        } else {
+            classes = split_step_timed(m, rho, s, label);
+        }
+        QED_CUDA_TRY(cudaEventSynchronize(m->ev[classes]));
+        for (int c = 0; c < classes; ++c) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, m->ev[c], m->ev[c + 1]);
+            acc[(size_t)c] += t;
+        }
+    }
+    if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
+    for (int c = 0; c < n_kernels; ++c) ms[c] = c < classes ? acc[(size_t)c] / (double)n_steps : 0.0;
+    if (names && name_cap > 0) {
+        std::strncpy(names, label.c_str(), (size_t)name_cap - 1);
+        names[name_cap - 1] = 0;
+    }
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    return QED_OK;
+}
+
+}  // extern "C"

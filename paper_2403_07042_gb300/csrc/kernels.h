@@ -1,0 +1,49 @@
+// Launchers of the device kernels (all enqueue on the given stream, no synchronisation).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace qed {
+
+// Number of kernels this library has launched (all launchers add to it).
+void count_launches(int64_t n);
+int64_t launches();
+
+// C = alpha * A * op(B) + beta * C for complex128 row-major matrices; op(B) = B (conj_b
+// false, B is K x N) or B^+ (conj_b true, B is N x K).  FP64 FMA, 32 x 32 tiles.
+void zgemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A,
+           int64_t lda, const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C,
+           int64_t ldc);
+
+// Y = c0 A + c1 B + c2 C + c3 I + c4 Y (real coefficients; any of A, B, C may be null).
+void zlincomb(cudaStream_t s, int64_t D, double c0, const double2 *A, double c1, const double2 *B,
+              double c2, const double2 *C, double c3, double c4, double2 *Y);
+
+// X = -i * theta * H
+void scale_minus_i(cudaStream_t s, int64_t D, double theta, const double2 *H, double2 *X);
+
+// aug (D x 2D) = [V - U | V + U]
+void pade_augment(cudaStream_t s, int64_t D, const double2 *Up, const double2 *Vp, double2 *aug);
+
+// Gauss-Jordan elimination with partial pivoting on aug = [Q | P]; afterwards the right
+// half holds Q^-1 P.  Sets kErrSingular in *err if a pivot is exactly zero.
+void gauss_jordan(cudaStream_t s, int64_t D, double2 *aug, uint32_t *err);
+
+// Copy the right half of aug (D x 2D) into R (D x D).
+void take_right_half(cudaStream_t s, int64_t D, const double2 *aug, double2 *R);
+
+// rho = V (1 - dt/2 (d_m + d_n)) + dt sum_j c_j(m) c_j(n) V[src_j(m), src_j(n)]
+void dissipate_f64(cudaStream_t s, int64_t D, const double2 *V, double2 *rho, const double *anti,
+                   const int32_t *in_ptr, const int32_t *in_jump, const int32_t *in_src,
+                   const double *in_coef, double dt);
+
+// out[o] = rho_kk (id < D), or sum_k w[id-D][k] rho_kk; deterministic block reduction.
+void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights,
+                 const int32_t *ids, int32_t n_obs, double *out);
+
+// rho <- (rho + rho^+) / (2 tr rho); flags non-finite traces in *err.
+void renormalise(cudaStream_t s, int64_t D, double2 *rho, double *scratch, uint32_t *err);
+
+}  // namespace qed

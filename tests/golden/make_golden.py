@@ -1,0 +1,48 @@
+"""Writes the stored oracle trajectories used by the full-length GPU parity tests.
+
+Calls only the FP64 oracle (and the seeded workload module).  Usage:
+    python tests/golden/make_golden.py hb_shaped_d512
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+import qed_workloads as W  # noqa: E402
+
+SAMPLED_ROWS = [0, 1, 2, 3, 64, 100, 255, 256, 300, 511]
+
+
+def hb_shaped_d512():
+    """The hydrogen-bond-shaped workload (dim 512), 10000 steps of dt 0.05: populations
+    every 100 steps and ten full rows of the final density matrix."""
+    m = W.hb_shaped()
+    b = oracle.enumerate_basis(m)
+    t0 = time.time()
+    rho, rec = oracle.evolve(m, basis=b, obs_ids=list(range(b.dim)))
+    np.savez_compressed(os.path.join(HERE, "hb_shaped_d512_oracle.npz"), records=rec,
+                        rho_rows=np.array(SAMPLED_ROWS), rho_sample=rho[SAMPLED_ROWS],
+                        trace=np.trace(rho).real, seconds=time.time() - t0)
+
+
+def lattice_32x32_d2049():
+    """The 32 x 32 lattice (dim 2049), 2000 steps of dt 0.1: the vacuum, photon and atom
+    populations every 100 steps (all 2049 diagonal entries) and rows of the final rho."""
+    m = W.lattice()
+    b = oracle.enumerate_basis(m)
+    t0 = time.time()
+    rho, rec = oracle.evolve(m, basis=b, obs_ids=list(range(b.dim)))
+    rows = [0, 1, 2, 1 + 2 * (16 * 32 + 16), 2 + 2 * (16 * 32 + 16), 2047, 2048]
+    np.savez_compressed(os.path.join(HERE, "lattice_32x32_d2049_oracle.npz"), records=rec,
+                        rho_rows=np.array(rows), rho_sample=rho[rows], trace=np.trace(rho).real,
+                        seconds=time.time() - t0)
+
+
+if __name__ == "__main__":
+    for name in sys.argv[1:]:
+        globals()[name]()

@@ -1,0 +1,161 @@
+"""GPU checks of the split-precision path: the tcgen05 product against an FP64 reference
+of the same three-term FP16 product, and the increment-form evolution against the FP64
+oracle (max|drho| <= 1e-5 and populations <= 1e-6, the bars of the method's accuracy
+contract)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import qed_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+qed = pytest.importorskip("paper_2403_07042_gb300")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RHO_TOL = 1e-5
+POP_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_07042_gb300 import build
+    build.build()
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _planes(rng, rows, K, scale):
+    x = rng.standard_normal((rows, K)) * scale
+    hi = x.astype(np.float16)
+    lo = (x - hi.astype(np.float64)).astype(np.float16)
+    return np.stack([hi, lo])
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 384, 512, 1), (256, 128, 1024, 3),
+                                          (384, 256, 256, 4)])
+def test_tc_gemm_three_term_product(M, N, K, splits):
+    """out = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T, checked elementwise against FP64
+    within the FP32 accumulation bound 3K * 2^-23 * (|A_hi| + |A_lo|)(|B_hi| + |B_lo|)^T."""
+    rng = np.random.default_rng(M + N + K + splits)
+    A = _planes(rng, M, K, 1.0)
+    B = _planes(rng, N, K, 1.0)
+    out = qed.tc_gemm(_cuda(A), _cuda(B), splits=splits).cpu().numpy().astype(np.float64)
+    Ah, Al = A[0].astype(np.float64), A[1].astype(np.float64)
+    Bh, Bl = B[0].astype(np.float64), B[1].astype(np.float64)
+    want = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    bound = 3 * K * 2.0 ** -23 * ((np.abs(Ah) + np.abs(Al)) @ (np.abs(Bh) + np.abs(Bl)).T)
+    got = out.sum(axis=0)
+    assert out.shape == (splits, M, N)
+    assert np.all(np.abs(got - want) <= bound)
+    # the three terms are really there: dropping A_lo or B_lo is detectable
+    assert np.abs(got - Ah @ Bh.T).max() > 10 * bound.max()
+
+
+def test_tc_gemm_rejects_bad_shapes():
+    a = torch.zeros((2, 100, 64), dtype=torch.float16, device="cuda")
+    b = torch.zeros((2, 128, 64), dtype=torch.float16, device="cuda")
+    with pytest.raises(qed.QedError):
+        qed.tc_gemm(a, b)
+
+
+def _evolve(model, n_steps, precision, rho0=None, U=None, record_every=0, obs=None):
+    b = oracle.enumerate_basis(model)
+    gm = qed.Model(model, precision=precision)
+    if U is not None:
+        gm.set_U(_cuda(U))
+    rho = _cuda(oracle.initial_density(model, b) if rho0 is None else rho0)
+    rec = gm.evolve(rho, n_steps, record_every=record_every, obs_ids=obs)
+    gm.sync()
+    return rho.cpu().numpy(), (None if rec is None else rec.cpu().numpy())
+
+
+@pytest.mark.parametrize("make,steps", [
+    (lambda: W.jch_two_cavities(), 2000),
+    (lambda: W.hb_shaped(), 500),
+    (lambda: W.lattice(6, 5, seed=7, gamma=5e-3), 300),
+    (lambda: W.chain_instance(np.random.default_rng(4), 100, 257), 300),
+])
+def test_split_parity_reduced_steps(make, steps):
+    """Split precision vs the oracle on several tiles and ragged dimensions."""
+    m = make()
+    b = oracle.enumerate_basis(m)
+    obs = list(range(b.dim))
+    rho_ref, rec_ref = oracle.evolve(m, n_steps=steps, record_every=50, basis=b, obs_ids=obs)
+    rho, rec = _evolve(m, steps, "split_fp16x2", record_every=50, obs=obs)
+    err, perr = np.abs(rho - rho_ref).max(), np.abs(rec - rec_ref).max()
+    print(f"{m['name']} D={b.dim} steps={steps}: max|drho|={err:.2e} max|dpop|={perr:.2e}")
+    assert err <= RHO_TOL and perr <= POP_TOL
+
+
+def test_split_random_mixed_state():
+    m = W.hb_shaped()
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=9)
+    rho_ref = oracle.evolve(m, rho0=rho0, n_steps=200, basis=b, return_records=False)
+    rho, _ = _evolve(m, 200, "split_fp16x2", rho0=rho0)
+    assert np.abs(rho - rho_ref).max() <= RHO_TOL
+
+
+def test_split_jch2_full_length():
+    """Two JC cavities (dim 36, padded to one 128 tile), all 20000 steps."""
+    m = W.jch_two_cavities()
+    b = oracle.enumerate_basis(m)
+    obs = list(range(b.dim))
+    rho_ref, rec_ref = oracle.evolve(m, basis=b, obs_ids=obs)
+    rho, rec = _evolve(m, m["n_steps"], "split_fp16x2", record_every=m["record_every"], obs=obs)
+    err, perr = np.abs(rho - rho_ref).max(), np.abs(rec - rec_ref).max()
+    print(f"jch2 split 20000 steps: max|drho|={err:.2e} max|dpop|={perr:.2e}")
+    assert err <= RHO_TOL and perr <= POP_TOL
+
+
+def test_split_hb_shaped_full_length_against_stored_oracle():
+    """The dim-512 workload at full length (10000 steps), in the configuration the bench
+    times, against the stored oracle trajectory (populations every 100 steps, ten rows of
+    the final rho), written by tests/golden/make_golden.py."""
+    path = os.path.join(GOLDEN, "hb_shaped_d512_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip("stored oracle trajectory not generated")
+    g = np.load(path)
+    m = W.hb_shaped()
+    rho, rec = _evolve(m, m["n_steps"], "split_fp16x2", record_every=m["record_every"],
+                       obs=list(range(512)))
+    err = np.abs(rho[g["rho_rows"]] - g["rho_sample"]).max()
+    perr = np.abs(rec - g["records"]).max()
+    print(f"hb_shaped split 10000 steps: max|drho| (sampled rows)={err:.2e} max|dpop|={perr:.2e}")
+    assert perr <= POP_TOL and err <= RHO_TOL
+    assert abs(np.trace(rho).real - 1.0) <= 1e-7
+    assert np.abs(rho - rho.conj().T).max() <= 1e-12
+
+
+def test_split_invariants_and_renormalisation():
+    m = W.hb_shaped()
+    b = oracle.enumerate_basis(m)
+    gm = qed.Model(m, precision="split_fp16x2")
+    gm.set_renorm_every(50)
+    rho = _cuda(W.random_density(b.dim, seed=3, rank=4))
+    gm.evolve(rho, 400)
+    gm.sync()
+    r = rho.cpu().numpy()
+    assert abs(np.trace(r).real - 1.0) <= 1e-12
+    assert np.abs(r - r.conj().T).max() <= 1e-15
+    assert np.linalg.eigvalsh(r).min() >= -1e-6
+
+
+def test_split_nonfinite_is_reported():
+    m = W.jch_two_cavities()
+    gm = qed.Model(m, precision="split_fp16x2")
+    gm.set_renorm_every(1)
+    rho = torch.zeros((36, 36), dtype=torch.complex128, device="cuda")
+    rho[0, 0] = float("nan")
+    gm.evolve(rho, 2)
+    with pytest.raises(qed.QedError) as ei:
+        gm.sync()
+    assert ei.value.status == qed.QED_ENUMERIC
