@@ -195,14 +195,17 @@ qed_status qed_profile(qed_model *m, void *rho, int64_t n_steps, double *ms, int
 
 /*
  * The tensor-core product of the split-precision step, exposed for testing:
- *     out[s] = sum over the K-slices of slice s of (A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T)
- * with A = a_planes (device FP16 [2][M][K], hi plane then lo plane, K contiguous) and
- * B = b_planes (device FP16 [2][N][K]); out is device FP32 [splits][M][N] (split-K partial
- * sums; their sum is the product).  M and N multiples of 128, K of 64, planes 16-byte
- * aligned.  tcgen05.mma (kind::f16, FP32 accumulation in tensor memory) fed by TMA.
- * Synchronises `stream`.  EINVAL on bad shapes, ETIMEOUT if a bounded wait ran out.
+ *     out[s] = sum over the K-slices of slice s of  sum_q A_{pa(q)} B_{pb(q)}^T
+ * with A = a_planes (device FP16 [planes_a][M][K], K contiguous), B = b_planes (device
+ * FP16 [planes_b][N][K]) and the n_seg (<= 6) plane pairs seg_pairs = {pa(0), pb(0), ...}
+ * (host int32), e.g. {0,0, 0,1, 1,0} for hi*hi + hi*lo + lo*hi.  out is device FP32
+ * [splits][M][N] (split-K partial sums; their sum is the product).  M and N multiples of
+ * 128, K of 64, planes 16-byte aligned.  tcgen05.mma (kind::f16, FP32 accumulation in
+ * tensor memory) fed by TMA.  Synchronises `stream`.  EINVAL on bad shapes or plane
+ * indices, ETIMEOUT if a bounded wait ran out.
  */
-qed_status qed_tc_gemm(const void *a_planes, const void *b_planes, int32_t M, int32_t N, int32_t K,
+qed_status qed_tc_gemm(const void *a_planes, int32_t planes_a, const void *b_planes, int32_t planes_b,
+                       int32_t M, int32_t N, int32_t K, int32_t n_seg, const int32_t *seg_pairs,
                        int32_t splits, float *out, qed_stream stream);
 
 /* Total number of kernels this library has launched in this process (all models). */

@@ -82,7 +82,7 @@ def lib():
         "qed_get_U": [vp, vp, vp],
         "qed_profile": [vp, vp, i64, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_launch_count": [ctypes.POINTER(i64)],
-        "qed_tc_gemm": [vp, vp, i32, i32, i32, i32, vp, vp],
+        "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -186,16 +186,19 @@ def launch_count():
     return n.value
 
 
-def tc_gemm(a_planes, b_planes, splits=1, stream=None):
-    """Split-K partial sums [splits, M, N] (FP32) of the three-term FP16 product of the
-    split-precision step; a_planes [2, M, K], b_planes [2, N, K] are CUDA float16."""
+def tc_gemm(a_planes, b_planes, segments=((0, 0), (0, 1), (1, 0)), splits=1, stream=None):
+    """Split-K partial sums [splits, M, N] (FP32) of sum over segments (p, q) of
+    A_p B_q^T, the FP16 tensor-core product of the split-precision step; a_planes
+    [planes, M, K] and b_planes [planes, N, K] are CUDA float16."""
     import torch
     M, K = a_planes.shape[1], a_planes.shape[2]
     N = b_planes.shape[1]
+    seg = _arr([x for pq in segments for x in pq], np.int32)
     out = torch.empty((splits, M, N), dtype=torch.float32, device=a_planes.device)
-    _check(lib().qed_tc_gemm(ctypes.c_void_p(a_planes.data_ptr()), ctypes.c_void_p(b_planes.data_ptr()),
-                             M, N, K, splits, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
-           "qed_tc_gemm")
+    _check(lib().qed_tc_gemm(ctypes.c_void_p(a_planes.data_ptr()), a_planes.shape[0],
+                             ctypes.c_void_p(b_planes.data_ptr()), b_planes.shape[0], M, N, K, len(segments),
+                             seg.ctypes.data_as(_c_int32_p), splits, ctypes.c_void_p(out.data_ptr()),
+                             _stream_handle(stream)), "qed_tc_gemm")
     return out
 
 

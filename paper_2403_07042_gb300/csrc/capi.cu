@@ -105,8 +105,11 @@ qed_status propagator(cudaStream_t s, int64_t D, double dt, const double2 *H, do
 
 void release(qed_model *m) {
     if (!m) return;
-    void *ptrs[] = {m->U, m->work1, m->work2, m->phase, m->anti, m->in_ptr, m->in_jump, m->in_src,
-                    m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err};
+    for (auto &g : m->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    void *ptrs[] = {m->U,      m->work1,  m->work2, m->phase,       m->anti,    m->in_ptr, m->in_jump,
+                    m->in_src, m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err,    m->rho_int};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->err_host) cudaFreeHost(m->err_host);
@@ -198,8 +201,6 @@ qed_status ensure_ids(qed_model *m, int32_t n_obs, const int32_t *ids, cudaStrea
 }
 
 
-}  // namespace
-
 // One FP64 step: V = (U rho) U^+, then the Lindblad update (Eq. 3) into rho.
 void step_f64(qed_model *m, double2 *rho, cudaStream_t s) {
     const int64_t D = m->D;
@@ -207,6 +208,75 @@ void step_f64(qed_model *m, double2 *rho, cudaStream_t s) {
     zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
     dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, m->dt);
 }
+
+void one_step(qed_model *m, cudaStream_t s) {
+    if (m->prec == QED_FP64)
+        step_f64(m, m->rho_int, s);
+    else
+        split_step(m, s);
+}
+
+constexpr int64_t kGraphSteps = 16;
+
+// Captures the step sequences (1 and kGraphSteps steps) into CUDA graphs on a
+// library-owned stream.  Falls back to direct launches if capture is unavailable.
+qed_status ensure_graphs(qed_model *m) {
+    if (m->graph[0] || m->graphs_off) return QED_OK;
+    if (!m->cap_stream) QED_CUDA_TRY(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+    const int64_t counts[2] = {1, kGraphSteps};
+    for (int g = 0; g < 2; ++g) {
+        const int64_t before = launches();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            m->graphs_off = true;
+            return QED_OK;
+        }
+        for (int64_t k = 0; k < counts[g]; ++k) one_step(m, m->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(m->cap_stream, &graph);
+        const int64_t captured = launches() - before;
+        count_launches(-captured);  // captured, not launched
+        if (e != cudaSuccess || !graph) {
+            cudaGetLastError();
+            m->graphs_off = true;
+            return QED_OK;
+        }
+        e = cudaGraphInstantiate(&m->graph[g], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            m->graph[g] = nullptr;
+            m->graphs_off = true;
+            return QED_OK;
+        }
+        m->graph_kernels[g] = captured;
+    }
+    return QED_OK;
+}
+
+// k consecutive steps with nothing to record or renormalise in between.
+qed_status run_steps(qed_model *m, int64_t k, cudaStream_t s) {
+    if (m->graphs_off) {
+        for (int64_t i = 0; i < k; ++i) one_step(m, s);
+        return QED_OK;
+    }
+    for (; k >= kGraphSteps; k -= kGraphSteps) {
+        QED_CUDA_TRY(cudaGraphLaunch(m->graph[1], s));
+        count_launches(m->graph_kernels[1]);
+    }
+    for (; k > 0; --k) {
+        QED_CUDA_TRY(cudaGraphLaunch(m->graph[0], s));
+        count_launches(m->graph_kernels[0]);
+    }
+    return QED_OK;
+}
+
+int64_t next_multiple_after(int64_t off, int64_t i, int64_t every) {
+    // smallest p > i with (off + p) % every == 0
+    return i + (every - (off + i) % every);
+}
+
+}  // namespace
 
 }  // namespace qed
 
@@ -375,23 +445,40 @@ qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_o
     cudaStream_t s = (cudaStream_t)stream;
     QED_TRY(ensure_ids(m, n_obs, obs_ids, s));
     double2 *rho = (double2 *)rho_v;
+    const int64_t D = m->D;
+    const bool split = m->prec != QED_FP64;
+    if (split) {
+        QED_TRY(split_begin(m, rho, s));
+    } else {
+        if (!m->rho_int) QED_TRY(dev_alloc(&m->rho_int, (size_t)(D * D)));
+        QED_CUDA_TRY(cudaMemcpyAsync(m->rho_int, rho, (size_t)(D * D) * 16, cudaMemcpyDeviceToDevice, s));
+    }
+    QED_TRY(ensure_graphs(m));
+    const bool renorm = split && m->renorm_every > 0;
     int64_t row = 0;
-    if (m->prec != QED_FP64) QED_TRY(split_begin(m, rho, s));
-    for (int64_t i = 0; i <= n_steps; ++i) {
-        if (n_obs > 0 && (step_offset + i) % record_every == 0) {
-            if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
-            observables(s, m->D, rho, m->obs_w, m->obs_ids_dev, n_obs, records + row * n_obs);
+    auto record = [&](int64_t p) {
+        if (n_obs > 0 && (step_offset + p) % record_every == 0) {
+            if (split)
+                split_observables(m, m->obs_ids_dev, n_obs, records + row * n_obs, s);
+            else
+                observables(s, D, m->rho_int, m->obs_w, m->obs_ids_dev, n_obs, records + row * n_obs);
             ++row;
         }
-        if (i == n_steps) break;
-        if (m->prec == QED_FP64) {
-            step_f64(m, rho, s);
-        } else {
-            split_step(m, rho, s);
-            if (m->renorm_every > 0 && (step_offset + i + 1) % m->renorm_every == 0) split_renorm(m, rho, s);
-        }
+    };
+    record(0);
+    for (int64_t i = 0; i < n_steps;) {
+        int64_t p = n_steps;
+        if (n_obs > 0) p = std::min(p, next_multiple_after(step_offset, i, record_every));
+        if (renorm) p = std::min(p, next_multiple_after(step_offset, i, m->renorm_every));
+        QED_TRY(run_steps(m, p - i, s));
+        i = p;
+        if (renorm && (step_offset + p) % m->renorm_every == 0) split_renorm(m, s);
+        record(p);
     }
-    if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
+    if (split)
+        split_end(m, rho, s);
+    else
+        QED_CUDA_TRY(cudaMemcpyAsync(rho, m->rho_int, (size_t)(D * D) * 16, cudaMemcpyDeviceToDevice, s));
     QED_CUDA_TRY(cudaGetLastError());
     return QED_OK;
 }
@@ -460,7 +547,7 @@ qed_status qed_profile(qed_model *m, void *rho_v, int64_t n_steps, double *ms, i
             classes = 3;
             label = "zgemm_f64_1,zgemm_f64_2,dissipate_f64";
         } else {
-            classes = split_step_timed(m, rho, s, label);
+            classes = split_step_timed(m, s, label);
         }
         QED_CUDA_TRY(cudaEventSynchronize(m->ev[classes]));
         for (int c = 0; c < classes; ++c) {
@@ -469,7 +556,7 @@ qed_status qed_profile(qed_model *m, void *rho_v, int64_t n_steps, double *ms, i
             acc[(size_t)c] += t;
         }
     }
-    if (m->prec != QED_FP64) split_sync_rho(m, rho, s);
+    if (m->prec != QED_FP64) split_end(m, rho, s);
     for (int c = 0; c < n_kernels; ++c) ms[c] = c < classes ? acc[(size_t)c] / (double)n_steps : 0.0;
     if (names && name_cap > 0) {
         std::strncpy(names, label.c_str(), (size_t)name_cap - 1);

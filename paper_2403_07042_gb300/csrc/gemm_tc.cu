@@ -2,7 +2,8 @@
 // "unitary evolution" stage (Sec. 4.2, Table 3) in split precision.
 //
 // One CTA computes one 128 x 128 FP32 tile of one split-K slice:
-//   warp 0, one lane : TMA producer, 6-stage ring of (A 128x64, B 128x64) FP16 tiles,
+//   warp 0, one lane : TMA producer, 6-stage ring of (A 128x64, B 128x64) FP16 tiles of the
+//                      current segment's planes,
 //                      128-byte swizzled, completion tracked by mbarrier transaction bytes
 //   warp 1, one lane : MMA issuer, tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
 //                      into a TMEM accumulator; tcgen05.commit frees each smem stage
@@ -124,6 +125,7 @@ struct Params {
     int kb_per_seg;
     int kb_total;
     int kb_per_split;
+    int seg_a[kTcMaxSeg], seg_b[kTcMaxSeg];
     float *out;
     uint32_t *err;
 };
@@ -186,8 +188,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             const int seg = kb / p.kb_per_seg, kk = kb % p.kb_per_seg;
             const uint32_t bar = full0 + 8 * s;
             mbar_expect_tx(bar, kStageA + kStageB);
-            tma_load_3d(smem_u32(sA + s * kStageA), &tmA, kk * kTcBK, tile_m * kTcBM, seg == 2 ? 1 : 0, bar);
-            tma_load_3d(smem_u32(sB + s * kStageB), &tmB, kk * kTcBK, tile_n * kTcBN, seg == 1 ? 1 : 0, bar);
+            tma_load_3d(smem_u32(sA + s * kStageA), &tmA, kk * kTcBK, tile_m * kTcBM, p.seg_a[seg], bar);
+            tma_load_3d(smem_u32(sB + s * kStageB), &tmB, kk * kTcBK, tile_n * kTcBN, p.seg_b[seg], bar);
             *issued = i + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -266,13 +268,13 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-bool encode(CUtensorMap *map, const void *base, int K, int rows, int box_rows) {
+bool encode(CUtensorMap *map, const void *base, int K, int rows, int planes, int box_rows) {
     EncodeTiled fn = encode_fn();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
         return false;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 2};
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * (cuuint64_t)rows};
     cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -292,18 +294,33 @@ size_t tc_gemm_smem_bytes() {
     return 1024 + (size_t)kTcStages * (kStageA + kStageB) + (2 * kTcStages + 1) * 8 + 32;
 }
 
-bool tc_gemm_plan(TcGemm &g, const void *a_planes, const void *b_planes, int M, int N, int K, int num_sms,
-                  int force_splits) {
+bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_planes, int planes_b, int M, int N,
+                  int K, int nseg, const int *seg_pairs, int num_sms, int force_splits) {
     if (M % kTcBM || N % kTcBN || K % kTcBK || ((uintptr_t)a_planes & 15) || ((uintptr_t)b_planes & 15)) {
         set_error("tc_gemm: shapes must be multiples of the tile and planes 16-byte aligned");
         return false;
     }
+    if (nseg < 1 || nseg > kTcMaxSeg || planes_a < 1 || planes_b < 1) {
+        set_error("tc_gemm: 1..6 segments and at least one plane per operand");
+        return false;
+    }
+    for (int q = 0; q < nseg; ++q) {
+        if (seg_pairs[2 * q] < 0 || seg_pairs[2 * q] >= planes_a || seg_pairs[2 * q + 1] < 0 ||
+            seg_pairs[2 * q + 1] >= planes_b) {
+            set_error("tc_gemm: segment plane index out of range");
+            return false;
+        }
+        g.seg_a[q] = seg_pairs[2 * q];
+        g.seg_b[q] = seg_pairs[2 * q + 1];
+    }
+    g.nseg = nseg;
     g.M = M;
     g.N = N;
     g.K = K;
-    if (!encode(&g.a, a_planes, K, M, kTcBM) || !encode(&g.b, b_planes, K, N, kTcBN)) return false;
+    if (!encode(&g.a, a_planes, K, M, planes_a, kTcBM) || !encode(&g.b, b_planes, K, N, planes_b, kTcBN))
+        return false;
     const int tiles = (M / kTcBM) * (N / kTcBN);
-    const int kb_total = 3 * (K / kTcBK);
+    const int kb_total = nseg * (K / kTcBK);
     int splits = num_sms / tiles;
     splits = splits < 1 ? 1 : splits;
     const int max_splits = kb_total / 8 > 0 ? kb_total / 8 : 1;  // at least 8 k-blocks per slice
@@ -329,7 +346,11 @@ void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) 
     p.M = g.M;
     p.N = g.N;
     p.kb_per_seg = g.K / kTcBK;
-    p.kb_total = 3 * p.kb_per_seg;
+    p.kb_total = g.nseg * p.kb_per_seg;
+    for (int q = 0; q < kTcMaxSeg; ++q) {
+        p.seg_a[q] = q < g.nseg ? g.seg_a[q] : 0;
+        p.seg_b[q] = q < g.nseg ? g.seg_b[q] : 0;
+    }
     p.kb_per_split = g.kb_per_split;
     p.out = out;
     p.err = err;
@@ -340,17 +361,20 @@ void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) 
 
 }  // namespace qed
 
-extern "C" qed_status qed_tc_gemm(const void *a_planes, const void *b_planes, int32_t M, int32_t N, int32_t K,
+extern "C" qed_status qed_tc_gemm(const void *a_planes, int32_t planes_a, const void *b_planes, int32_t planes_b,
+                                  int32_t M, int32_t N, int32_t K, int32_t n_seg, const int32_t *seg_pairs,
                                   int32_t splits, float *out, qed_stream stream) {
     using namespace qed;
-    if (!a_planes || !b_planes || !out || M <= 0 || N <= 0 || K <= 0 || splits <= 0) {
+    if (!a_planes || !b_planes || !out || !seg_pairs || M <= 0 || N <= 0 || K <= 0 || splits <= 0) {
         set_error("qed_tc_gemm: bad argument");
         return QED_EINVAL;
     }
     TcGemm g;
-    if (!tc_gemm_plan(g, a_planes, b_planes, M, N, K, 1, splits)) return QED_EINVAL;
+    int pairs[2 * kTcMaxSeg];
+    for (int q = 0; q < 2 * n_seg && q < 2 * kTcMaxSeg; ++q) pairs[q] = seg_pairs[q];
+    if (!tc_gemm_plan(g, a_planes, planes_a, b_planes, planes_b, M, N, K, n_seg, pairs, 1, splits)) return QED_EINVAL;
     if (g.splits != splits) {
-        set_error("qed_tc_gemm: splits must divide the 3K/64 k-blocks into that many non-empty slices");
+        set_error("qed_tc_gemm: splits must divide the n_seg*K/64 k-blocks into that many non-empty slices");
         return QED_EINVAL;
     }
     uint32_t *err = nullptr;

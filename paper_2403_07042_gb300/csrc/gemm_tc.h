@@ -8,14 +8,19 @@
 
 namespace qed {
 
-// Operands are FP16, K-major, stored as [2 planes (hi, lo)][rows][K].  The kernel computes
-//   C[M x N] = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
-// as one K loop over three segments (the lo*lo product is dropped), accumulating in FP32
-// in tensor memory, and writes split-K partial sums out[split][M][N] (FP32).
+// Operands are FP16, K-major, stored as [planes][rows][K] (the pieces of an FP64 value:
+// hi, then lo, or hi, mid, lo).  The kernel computes
+//   C[M x N] = sum over segments s of A_{pa(s)} B_{pb(s)}^T
+// as one K loop over the segments (e.g. hi*hi + hi*lo + lo*hi), accumulating in FP32 in
+// tensor memory, and writes split-K partial sums out[split][M][N] (FP32).
+constexpr int kTcMaxSeg = 6;
+
 struct TcGemm {
-    CUtensorMap a;      // dims (K, M, 2), box (64, 128, 1), 128-byte swizzle
-    CUtensorMap b;      // dims (K, N, 2), box (64, BN, 1)
+    CUtensorMap a;      // dims (K, M, planes_a), box (64, 128, 1), 128-byte swizzle
+    CUtensorMap b;      // dims (K, N, planes_b), box (64, BN, 1)
     int M = 0, N = 0, K = 0;
+    int nseg = 0;
+    int seg_a[kTcMaxSeg] = {}, seg_b[kTcMaxSeg] = {};
     int splits = 1;
     int kb_per_split = 0;
 };
@@ -27,8 +32,8 @@ constexpr int kTcStages = 6;
 
 // Encodes the two tensor maps and picks the split-K factor for `num_sms`.
 // Returns false (with an error message set) if the driver entry point is unavailable.
-bool tc_gemm_plan(TcGemm &g, const void *a_planes, const void *b_planes, int M, int N, int K, int num_sms,
-                  int force_splits = 0);
+bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_planes, int planes_b, int M, int N,
+                  int K, int nseg, const int *seg_pairs, int num_sms, int force_splits = 0);
 
 // Launch on `s`; `err` receives kErrTimeout if a bounded wait ran out.
 void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s);

@@ -30,25 +30,8 @@ enum : uint32_t {
     kErrTimeout = 4u,
 };
 
-// Operand planes of the split-precision (increment form) path.
-struct SplitPlanes {
-    int64_t Dp = 0;            // padded dimension (multiple of 128)
-    // static operands, FP16 [2 (hi, lo)][2Dp][2Dp]
-    void *a1 = nullptr;        // [[Dre, Dim], [Dim, -Dre]]      (GEMM1 A, rows k / k+Dp)
-    void *b2 = nullptr;        // [[Dre, Dim], [-Dim, Dre]]      (GEMM2 B, rows l / l+Dp)
-    // dynamic operands
-    void *rho_pl = nullptr;    // FP16 [2][Dp][2Dp]   rows l: [rho_re | rho_im]
-    void *w_pl = nullptr;      // FP16 [2][Dp][2Dp]   rows k: [W_re | W_im]
-    float *w32 = nullptr;      // FP32 [2][Dp][Dp]    W = Delta rho (re plane, im plane)
-    float *x32 = nullptr;      // FP32 [Dp][2Dp]      X = W Delta^+ (cols re | im)
-    float *partial = nullptr;  // split-K partial sums
-    int64_t partial_elems = 0;
-    double scale_delta = 1.0;  // power-of-two scales applied before the FP16 split
-    double scale_rho = 1.0;
-    double scale_w = 1.0;
-    void *tmaps = nullptr;     // device copy of the TMA descriptors (CUtensorMap[4])
-    std::vector<unsigned char> tmap_host;
-};
+// State of the split-precision (increment form) path; defined in split.cu.
+struct SplitState;
 
 }  // namespace qed
 
@@ -81,6 +64,13 @@ struct qed_model {
     uint32_t *err = nullptr;          // device error word
     uint32_t *err_host = nullptr;     // pinned mirror
 
-    qed::SplitPlanes sp;
+    qed::SplitState *sp = nullptr;
     cudaEvent_t ev[16] = {};
+
+    // step loop as CUDA graphs: graph[0] runs 1 step, graph[1] runs kGraphSteps steps
+    double2 *rho_int = nullptr;       // FP64 path: the state the graphs step in place
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
+    bool graphs_off = false;          // set if capture is unavailable (direct launches)
 };

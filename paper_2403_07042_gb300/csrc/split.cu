@@ -3,14 +3,21 @@
 // With E_k = H_kk and P = diag(exp(-i E_k dt)), the propagator factors exactly as
 // U = P (I + Delta), Delta = P^-1 U - I, so the "unitary evolution" of Sec. 4.2 is
 //     V = U rho U^+ = P (rho + W + W^+ + X) P^+,   W = Delta rho,  X = W Delta^+.
-// rho stays FP64; only the small increments W and X go through the tensor cores, with
-// every operand split into an FP16 hi part and an FP16 lo part (power-of-two scaled) and
-// the three products hi*hi + hi*lo + lo*hi accumulated in FP32.  Complex products use
-// the real embedding, with the signs folded into the constant operands:
+// Only the small increments W and X go through the tensor cores: every operand is split
+// into power-of-two scaled FP16 pieces (rho and W: hi + lo; the constant Delta: hi + mid +
+// lo, because its representation error would otherwise add up coherently step after
+// step) and the products that matter at 2^-22 are accumulated in FP32 (GEMM1: four,
+// GEMM2: three).  Complex products use the real embedding with the signs folded into the
+// constant operands:
 //   GEMM1  [W_re; W_im] (2Dp x Dp)  = [[D_re, D_im], [D_im, -D_re]] . [rho_re | rho_im]^T
 //   GEMM2  [X_re | X_im] (Dp x 2Dp) = [W_re | W_im] . [[D_re, D_im], [-D_im, D_re]]^T
 // (rho^T = conj(rho) for the Hermitian rho, so the row-major rho planes are the K-major
-// operand directly.)  The Lindblad update of Eq. (3) then runs on V in FP64.
+// operand directly.)
+//
+// The master rho is held as a double-float (an unevaluated sum of two FP32 words, about
+// 48 significant bits): GB300 executes FP64 at a small fraction of its FP32 rate, so the
+// per-step element work (forming V, the phase, the Lindblad update of Eq. 3, the next
+// FP16 planes) runs entirely in FP32 arithmetic with error-free transformations.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -24,13 +31,97 @@
 
 namespace qed {
 
+struct SplitState {
+    int64_t Dp = 0;           // padded dimension (multiple of 128)
+    int num_sms = 148;
+    TcGemm g1, g2;
+    // constant operands, FP16 [3 (hi, mid, lo)][2Dp][2Dp]
+    __half *a1 = nullptr;     // [[Dre, Dim], [Dim, -Dre]]   (GEMM1 A)
+    __half *b2 = nullptr;     // [[Dre, Dim], [-Dim, Dre]]   (GEMM2 B)
+    // dynamic operands, FP16 [2 (hi, lo)][Dp][2Dp]
+    __half *rho_pl = nullptr; // rows l: [rho_re | rho_im]
+    __half *w_pl = nullptr;   // rows k: [W_re | W_im]
+    float *w32 = nullptr;     // [2][Dp][Dp]  W (re plane, im plane)
+    float *wt32 = nullptr;    // [2][Dp][Dp]  W^T (re plane, im plane)
+    float *partial = nullptr; // split-K partial sums of either product
+    float4 *rho_df[2] = {nullptr, nullptr};  // D x D {re_hi, re_lo, im_hi, im_lo}: rho, then V
+    float4 *phase_df = nullptr;              // D: P_k as {re_hi, re_lo, im_hi, im_lo}
+    float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
+    float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
+    double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
+};
+
 namespace {
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-__device__ __forceinline__ void split_half(double x, __half &hi, __half &lo) {
+// ------------------------------------------------------------------ double-float
+// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based TwoProd).
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    df s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+struct cdf {
+    df re, im;
+};
+
+__device__ __forceinline__ cdf load_cdf(const float4 &v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 store_cdf(const cdf &c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
+
+__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
+    return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+
+__device__ __forceinline__ cdf cdf_mul_conj(cdf a, cdf b) {  // a * conj(b)
+    return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.im, b.re), df_neg(df_mul(a.re, b.im)))};
+}
+
+// FP16 hi/lo pieces of a scaled double-float value, in FP32 arithmetic: x = hi + lo.
+__device__ __forceinline__ void df_to_half2(df x, float s, __half &h, __half &l) {
+    const float xs = x.hi * s;  // power-of-two scaling is exact
+    h = __float2half_rn(xs);
+    l = __float2half_rn(__fadd_rn(__fsub_rn(xs, __half2float(h)), x.lo * s));
+}
+
+// ------------------------------------------------------------------ set-up kernels
+__device__ __forceinline__ void split_half3(double x, __half &hi, __half &mid, __half &lo) {
     hi = __double2half(x);
-    lo = __double2half(x - (double)__half2float(hi));
+    double r = x - (double)__half2float(hi);
+    mid = __double2half(r);
+    lo = __double2half(r - (double)__half2float(mid));
 }
 
 // Delta = conj(P_k) U_kl - delta_kl   (|P_k| = 1, so P^-1 = conj(P))
@@ -44,7 +135,8 @@ __global__ void make_delta_kernel(int64_t D, const double2 *U, const double2 *P,
     Dl[idx] = d;
 }
 
-// a1 = [[Dre, Dim], [Dim, -Dre]] and b2 = [[Dre, Dim], [-Dim, Dre]], 2Dp x 2Dp, hi/lo planes.
+// a1 = [[Dre, Dim], [Dim, -Dre]] and b2 = [[Dre, Dim], [-Dim, Dre]] (2Dp x 2Dp) as three
+// FP16 planes (hi, mid, lo), about 33 significant bits.
 __global__ void static_planes_kernel(int64_t D, int64_t Dp, const double2 *Dl, double s, __half *a1, __half *b2) {
     const int64_t W2 = 2 * Dp;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,111 +152,251 @@ __global__ void static_planes_kernel(int64_t D, int64_t Dp, const double2 *Dl, d
         else if (rlo && !clo) { va = d.y; vb = -d.y; }
         else { va = -d.x; vb = d.x; }
     }
-    __half h, l;
-    split_half(va * s, h, l);
+    __half h, md, l;
+    split_half3(va * s, h, md, l);
     a1[idx] = h;
-    a1[W2 * W2 + idx] = l;
-    split_half(vb * s, h, l);
+    a1[W2 * W2 + idx] = md;
+    a1[2 * W2 * W2 + idx] = l;
+    split_half3(vb * s, h, md, l);
     b2[idx] = h;
-    b2[W2 * W2 + idx] = l;
+    b2[W2 * W2 + idx] = md;
+    b2[2 * W2 * W2 + idx] = l;
 }
 
-// rho planes: row l = [rho_re[l, :] | rho_im[l, :]] (Dp x 2Dp), scaled, hi/lo.
-__global__ void rho_planes_kernel(int64_t D, int64_t Dp, const double2 *rho, double s, __half *pl) {
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t l = blockIdx.y;
-    if (m >= D || l >= D) return;
-    double2 v = rho[l * D + m];
-    __half h, lo;
+// ------------------------------------------------------------------ per-evolve kernels
+// caller rho (FP64) -> double-float state and the FP16 planes of GEMM1's B operand
+__global__ void import_kernel(int64_t D, int64_t Dp, const double2 *rho, float s, float4 *st, __half *pl) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = blockIdx.y;
+    if (n >= D) return;
+    const double2 v = rho[m * D + n];
+    const float rh = (float)v.x, ih = (float)v.y;
+    const df re = {rh, (float)(v.x - (double)rh)}, im = {ih, (float)(v.y - (double)ih)};
+    st[m * D + n] = make_float4(re.hi, re.lo, im.hi, im.lo);
     const int64_t plane = Dp * 2 * Dp;
-    split_half(v.x * s, h, lo);
-    pl[l * 2 * Dp + m] = h;
-    pl[plane + l * 2 * Dp + m] = lo;
-    split_half(v.y * s, h, lo);
-    pl[l * 2 * Dp + Dp + m] = h;
-    pl[plane + l * 2 * Dp + Dp + m] = lo;
+    __half h, l;
+    df_to_half2(re, s, h, l);
+    pl[m * 2 * Dp + n] = h;
+    pl[plane + m * 2 * Dp + n] = l;
+    df_to_half2(im, s, h, l);
+    pl[m * 2 * Dp + Dp + n] = h;
+    pl[plane + m * 2 * Dp + Dp + n] = l;
 }
 
-// W = sum of the split-K partials of GEMM1 (rows r < Dp real, r >= Dp imaginary), in FP32,
-// and its hi/lo planes as GEMM2's A operand: row k = [W_re[k, :] | W_im[k, :]].
-__global__ void w_reduce_kernel(int64_t Dp, int splits, const float *part, double inv_scale, double s_w, float *w32,
-                                __half *wpl) {
-    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t r = blockIdx.y;
-    if (l >= Dp) return;
-    const int64_t stride = 2 * Dp * Dp;
-    double acc = 0.0;
-    for (int s = 0; s < splits; ++s) acc += (double)part[s * stride + r * Dp + l];
-    const double w = acc * inv_scale;
-    w32[r * Dp + l] = (float)w;
-    const int64_t k = r % Dp;
-    const int64_t col = (r >= Dp ? Dp : 0) + l;
-    __half h, lo;
-    split_half(w * s_w, h, lo);
-    wpl[k * 2 * Dp + col] = h;
-    wpl[Dp * 2 * Dp + k * 2 * Dp + col] = lo;
+__global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * D) return;
+    const float4 v = st[idx];
+    rho[idx] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
 }
 
-// V_kl = P_k conj(P_l) (rho_kl + W_kl + conj(W_lk) + X_kl)
-__global__ void form_v_kernel(int64_t D, int64_t Dp, int splits, const double2 *__restrict__ rho,
-                              const float *__restrict__ w32, const float *__restrict__ part, double inv_scale,
-                              const double2 *__restrict__ P, double2 *__restrict__ V) {
-    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t k = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    if (k >= D || l >= D) return;
-    const int64_t stride = Dp * 2 * Dp;
-    double xr = 0.0, xi = 0.0;
-    for (int s = 0; s < splits; ++s) {
-        xr += (double)part[s * stride + k * 2 * Dp + l];
-        xi += (double)part[s * stride + k * 2 * Dp + Dp + l];
+// W from the split-K partials of GEMM1 (rows r < Dp real, r >= Dp imaginary), in FP32:
+// writes W, its transpose (through a shared-memory tile so both stores coalesce) and its
+// FP16 hi/lo planes as GEMM2's A operand, row k = [W_re[k, :] | W_im[k, :]].
+__global__ void __launch_bounds__(256) w_reduce_kernel(int64_t Dp, int splits, const float *__restrict__ part,
+                                                       float inv_scale, float s_w, float *__restrict__ w32,
+                                                       float *__restrict__ wt32, __half *__restrict__ wpl) {
+    __shared__ float tre[32][33], tim[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int64_t k0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
+    const int64_t stride = 2 * Dp * Dp, plane = Dp * 2 * Dp;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t k = k0 + ty + 8 * q, l = l0 + tx;
+        float re = 0.f, im = 0.f;
+        for (int s = 0; s < splits; ++s) {
+            re += part[s * stride + k * Dp + l];
+            im += part[s * stride + (Dp + k) * Dp + l];
+        }
+        re *= inv_scale;
+        im *= inv_scale;
+        w32[k * Dp + l] = re;
+        w32[Dp * Dp + k * Dp + l] = im;
+        tre[ty + 8 * q][tx] = re;
+        tim[ty + 8 * q][tx] = im;
+        const float xr = re * s_w, xi = im * s_w;
+        __half h = __float2half_rn(xr);
+        wpl[k * 2 * Dp + l] = h;
+        wpl[plane + k * 2 * Dp + l] = __float2half_rn(xr - __half2float(h));
+        h = __float2half_rn(xi);
+        wpl[k * 2 * Dp + Dp + l] = h;
+        wpl[plane + k * 2 * Dp + Dp + l] = __float2half_rn(xi - __half2float(h));
     }
-    const double2 r = rho[k * D + l];
-    double sr = r.x + (double)w32[k * Dp + l] + (double)w32[l * Dp + k] + xr * inv_scale;
-    double si = r.y + (double)w32[Dp * Dp + k * Dp + l] - (double)w32[Dp * Dp + l * Dp + k] + xi * inv_scale;
-    const double2 pk = P[k], pl = P[l];
-    // phase = P_k conj(P_l)
-    const double2 ph = make_double2(pk.x * pl.x + pk.y * pl.y, pk.y * pl.x - pk.x * pl.y);
-    V[k * D + l] = make_double2(ph.x * sr - ph.y * si, ph.x * si + ph.y * sr);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t l = l0 + ty + 8 * q, k = k0 + tx;
+        wt32[l * Dp + k] = tre[tx][ty + 8 * q];
+        wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + 8 * q];
+    }
 }
 
-// Lindblad update of Eq. (3) on V (as in the FP64 path) that also writes the rho planes.
-__global__ void dissipate_split_kernel(int64_t D, int64_t Dp, const double2 *__restrict__ V, double2 *__restrict__ rho,
-                                       const double *__restrict__ anti, const int32_t *__restrict__ in_ptr,
-                                       const int32_t *__restrict__ in_jump, const int32_t *__restrict__ in_src,
-                                       const double *__restrict__ in_coef, double dt, double s_rho,
-                                       __half *__restrict__ pl) {
+struct FormArgs {
+    int64_t D, Dp;
+    int splits;
+    const float4 *rho;
+    float4 *V;
+    const float *w32, *wt32, *part;
+    float inv_x;  // 1 / (s_W s_Delta)
+    const float4 *phase;
+};
+
+// V_mn = P_m conj(P_n) (rho_mn + W_mn + conj(W_nm) + X_mn): the increment in FP32, the
+// sum and the phase in double-float.
+__global__ void __launch_bounds__(256) form_v_kernel(FormArgs a) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    if (m >= D || n >= D) return;
-    double2 v = V[m * D + n];
-    double f = 1.0 - 0.5 * dt * (anti[m] + anti[n]);
-    double2 out = make_double2(v.x * f, v.y * f);
-    int a = in_ptr[m], ae = in_ptr[m + 1];
-    int b = in_ptr[n], be = in_ptr[n + 1];
-    while (a < ae && b < be) {
-        int ja = in_jump[a], jb = in_jump[b];
-        if (ja < jb) {
-            ++a;
-        } else if (ja > jb) {
-            ++b;
+    if (m >= a.D || n >= a.D) return;
+    const int64_t Dp = a.Dp, stride = Dp * 2 * Dp;
+    float xr = 0.f, xi = 0.f;
+    for (int s = 0; s < a.splits; ++s) {
+        xr += a.part[s * stride + m * 2 * Dp + n];
+        xi += a.part[s * stride + m * 2 * Dp + Dp + n];
+    }
+    const float ir = a.w32[m * Dp + n] + a.wt32[m * Dp + n] + xr * a.inv_x;
+    const float ii = a.w32[Dp * Dp + m * Dp + n] - a.wt32[Dp * Dp + m * Dp + n] + xi * a.inv_x;
+    cdf r = load_cdf(a.rho[m * a.D + n]);
+    r.re = df_add_f(r.re, ir);
+    r.im = df_add_f(r.im, ii);
+    const cdf pm = load_cdf(a.phase[m]), pn = load_cdf(a.phase[n]);
+    a.V[m * a.D + n] = store_cdf(cdf_mul(cdf_mul_conj(pm, pn), r));
+}
+
+struct DissArgs {
+    int64_t D, Dp;
+    const float4 *V;
+    float4 *rho;
+    const float2 *damp;
+    const int32_t *in_ptr, *in_jump, *in_src;
+    const float2 *coef;
+    float s_rho;
+    __half *pl;
+};
+
+// Eq. (3) on V: rho_mn = V_mn - (dt/2)(d_m + d_n) V_mn + dt sum_j c_j(m) c_j(n) V[src_j(m), src_j(n)];
+// the two correction terms (relative size dt gamma) are formed to FP32 accuracy and added
+// to the double-float V.  Also writes the FP16 planes of rho for the next GEMM1.
+__global__ void __launch_bounds__(256) dissipate_df_kernel(DissArgs a) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (m >= a.D || n >= a.D) return;
+    const int64_t D = a.D;
+    const cdf v = load_cdf(a.V[m * D + n]);
+    const float2 dm = a.damp[m], dn = a.damp[n];
+    const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
+    float gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
+    float gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
+    int p = a.in_ptr[m], pe = a.in_ptr[m + 1];
+    int q = a.in_ptr[n], qe = a.in_ptr[n + 1];
+    while (p < pe && q < qe) {  // jumps present in both incoming lists
+        const int jp = a.in_jump[p], jq = a.in_jump[q];
+        if (jp < jq) {
+            ++p;
+        } else if (jp > jq) {
+            ++q;
         } else {
-            double c = dt * in_coef[a] * in_coef[b];
-            double2 g = V[(int64_t)in_src[a] * D + in_src[b]];
-            out.x = fma(c, g.x, out.x);
-            out.y = fma(c, g.y, out.y);
-            ++a;
-            ++b;
+            const float2 cp = a.coef[p], cq = a.coef[q];
+            const df c = df_mul({cp.x, cp.y}, {cq.x, cq.y});  // dt c_j(m) c_j(n)
+            const float4 u = a.V[(int64_t)a.in_src[p] * D + a.in_src[q]];
+            const float ur = u.x + u.y, ui = u.z + u.w;
+            gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
+            gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
+            ++p;
+            ++q;
         }
     }
-    rho[m * D + n] = out;
-    __half h, lo;
+    cdf out;
+    out.re = df_add_f(v.re, gr);
+    out.im = df_add_f(v.im, gi);
+    a.rho[m * D + n] = store_cdf(out);
+    const int64_t plane = a.Dp * 2 * a.Dp;
+    __half h, l;
+    df_to_half2(out.re, a.s_rho, h, l);
+    a.pl[m * 2 * a.Dp + n] = h;
+    a.pl[plane + m * 2 * a.Dp + n] = l;
+    df_to_half2(out.im, a.s_rho, h, l);
+    a.pl[m * 2 * a.Dp + a.Dp + n] = h;
+    a.pl[plane + m * 2 * a.Dp + a.Dp + n] = l;
+}
+
+__global__ void __launch_bounds__(256) observables_df_kernel(int64_t D, const float4 *st, const double *w,
+                                                             const int32_t *ids, double *out) {
+    __shared__ double part[256];
+    const int o = blockIdx.x;
+    const int id = ids[o];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    if (id < D) {
+        if (t == 0) {
+            const float4 v = st[(int64_t)id * D + id];
+            s = (double)v.x + (double)v.y;
+        }
+    } else {
+        const double *wr = w + (int64_t)(id - D) * D;
+        for (int64_t k = t; k < D; k += blockDim.x) {
+            const float4 v = st[k * D + k];
+            s += wr[k] * ((double)v.x + (double)v.y);
+        }
+    }
+    part[t] = s;
+    __syncthreads();
+    for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+        if (t < st2) part[t] += part[t + st2];
+        __syncthreads();
+    }
+    if (t == 0) out[o] = part[0];
+}
+
+__global__ void __launch_bounds__(1024) trace_df_kernel(int64_t D, const float4 *st, double *tr, uint32_t *err) {
+    __shared__ double part[1024];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int64_t k = t; k < D; k += blockDim.x) {
+        const float4 v = st[k * D + k];
+        s += (double)v.x + (double)v.y;
+    }
+    part[t] = s;
+    __syncthreads();
+    for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+        if (t < st2) part[t] += part[t + st2];
+        __syncthreads();
+    }
+    if (t == 0) {
+        *tr = part[0];
+        if (!isfinite(part[0]) || !(part[0] > 0.0)) atomicOr(err, kErrNonFinite);
+    }
+}
+
+// rho <- (rho + rho^+) / (2 tr rho) on the double-float state (FP64 arithmetic; it runs
+// once every `renorm_every` steps), then the FP16 planes again.
+__global__ void symmetrise_df_kernel(int64_t D, int64_t Dp, float4 *st, const double *tr, const uint32_t *err,
+                                     float s_rho, __half *pl) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= D || j >= D || j < i) return;
+    if (*err & kErrNonFinite) return;
+    const double inv = 1.0 / *tr;
+    const float4 a = st[i * D + j], b = st[j * D + i];
+    double re = 0.5 * (((double)a.x + (double)a.y) + ((double)b.x + (double)b.y)) * inv;
+    double im = 0.5 * (((double)a.z + (double)a.w) - ((double)b.z + (double)b.w)) * inv;
+    if (i == j) im = 0.0;
+    const float rh = (float)re, ih = (float)im;
+    const df dre = {rh, (float)(re - (double)rh)}, dim = {ih, (float)(im - (double)ih)};
+    st[i * D + j] = make_float4(dre.hi, dre.lo, dim.hi, dim.lo);
+    st[j * D + i] = make_float4(dre.hi, dre.lo, -dim.hi, -dim.lo);
     const int64_t plane = Dp * 2 * Dp;
-    split_half(out.x * s_rho, h, lo);
-    pl[m * 2 * Dp + n] = h;
-    pl[plane + m * 2 * Dp + n] = lo;
-    split_half(out.y * s_rho, h, lo);
-    pl[m * 2 * Dp + Dp + n] = h;
-    pl[plane + m * 2 * Dp + Dp + n] = lo;
+    __half h, l;
+    df_to_half2(dre, s_rho, h, l);
+    pl[i * 2 * Dp + j] = h;
+    pl[plane + i * 2 * Dp + j] = l;
+    pl[j * 2 * Dp + i] = h;
+    pl[plane + j * 2 * Dp + i] = l;
+    df_to_half2(dim, s_rho, h, l);
+    pl[i * 2 * Dp + Dp + j] = h;
+    pl[plane + i * 2 * Dp + Dp + j] = l;
+    df_to_half2(df_neg(dim), s_rho, h, l);
+    pl[j * 2 * Dp + Dp + i] = h;
+    pl[plane + j * 2 * Dp + Dp + i] = l;
 }
 
 double pow2_scale(double maxabs, int target_exp) {
@@ -173,52 +405,132 @@ double pow2_scale(double maxabs, int target_exp) {
     return std::ldexp(1.0, target_exp - e);
 }
 
-struct SplitState {
-    TcGemm g1, g2;
-    int num_sms = 148;
-};
+template <class T>
+qed_status alloc(T **p, size_t count) {
+    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc failed for the split-precision buffers");
+        return QED_ENOMEM;
+    }
+    return QED_OK;
+}
 
-SplitState *state(qed_model *m) { return (SplitState *)m->sp.tmaps; }
+#define SPLIT_TRY(expr)                 \
+    do {                                \
+        qed_status st_ = (expr);        \
+        if (st_ != QED_OK) return st_;  \
+    } while (0)
+
+void launch_w_reduce(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    dim3 grid((unsigned)(S.Dp / 32), (unsigned)(S.Dp / 32));
+    w_reduce_kernel<<<grid, dim3(32, 8), 0, s>>>(S.Dp, S.g1.splits, S.partial,
+                                                 (float)(1.0 / (S.scale_delta * S.scale_rho)), (float)S.scale_w,
+                                                 S.w32, S.wt32, S.w_pl);
+    count_launches(1);
+}
+
+void launch_form(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    FormArgs a;
+    a.D = m->D;
+    a.Dp = S.Dp;
+    a.splits = S.g2.splits;
+    a.rho = S.rho_df[0];
+    a.V = S.rho_df[1];
+    a.w32 = S.w32;
+    a.wt32 = S.wt32;
+    a.part = S.partial;
+    a.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
+    a.phase = S.phase_df;
+    dim3 block(32, 8);
+    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
+    form_v_kernel<<<grid, block, 0, s>>>(a);
+    count_launches(1);
+}
+
+void launch_dissipate(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    DissArgs a;
+    a.D = m->D;
+    a.Dp = S.Dp;
+    a.V = S.rho_df[1];
+    a.rho = S.rho_df[0];
+    a.damp = S.damp_df;
+    a.in_ptr = m->in_ptr;
+    a.in_jump = m->in_jump;
+    a.in_src = m->in_src;
+    a.coef = S.coef_df;
+    a.s_rho = (float)S.scale_rho;
+    a.pl = S.rho_pl;
+    dim3 block(32, 8);
+    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
+    dissipate_df_kernel<<<grid, block, 0, s>>>(a);
+    count_launches(1);
+}
 
 }  // namespace
 
 qed_status split_prepare(qed_model *m, cudaStream_t s) {
-    SplitPlanes &sp = m->sp;
     const int64_t D = m->D;
     const int64_t Dp = (D + kTcBM - 1) / kTcBM * kTcBM;
     const size_t W2 = (size_t)(2 * Dp) * (size_t)(2 * Dp);
-    if (!sp.tmaps) {
-        SplitState *st = new SplitState();
-        sp.tmaps = st;
+    if (!m->sp) {
+        m->sp = new SplitState();
+        SplitState &S = *m->sp;
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, dev);
-        sp.Dp = Dp;
-        auto alloc = [&](void **p, size_t bytes) -> qed_status {
-            if (cudaMalloc(p, bytes) != cudaSuccess) {
-                cudaGetLastError();
-                set_error("cudaMalloc failed for the split-precision buffers");
-                return QED_ENOMEM;
-            }
-            return QED_OK;
-        };
-        qed_status st_;
-        if ((st_ = alloc(&sp.a1, W2 * 2 * sizeof(__half))) != QED_OK) return st_;
-        if ((st_ = alloc(&sp.b2, W2 * 2 * sizeof(__half))) != QED_OK) return st_;
-        if ((st_ = alloc(&sp.rho_pl, (size_t)Dp * 2 * Dp * 2 * sizeof(__half))) != QED_OK) return st_;
-        if ((st_ = alloc(&sp.w_pl, (size_t)Dp * 2 * Dp * 2 * sizeof(__half))) != QED_OK) return st_;
-        if ((st_ = alloc((void **)&sp.w32, (size_t)2 * Dp * Dp * sizeof(float))) != QED_OK) return st_;
-        QED_CUDA_TRY(cudaMemset(sp.rho_pl, 0, (size_t)Dp * 2 * Dp * 2 * sizeof(__half)));
-        QED_CUDA_TRY(cudaMemset(sp.w_pl, 0, (size_t)Dp * 2 * Dp * 2 * sizeof(__half)));
-        QED_CUDA_TRY(cudaMemset(sp.w32, 0, (size_t)2 * Dp * Dp * sizeof(float)));
-        if (!tc_gemm_plan(st->g1, sp.a1, sp.rho_pl, (int)(2 * Dp), (int)Dp, (int)(2 * Dp), st->num_sms))
+        cudaDeviceGetAttribute(&S.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        S.Dp = Dp;
+        const size_t pl = (size_t)Dp * 2 * Dp * 2;
+        SPLIT_TRY(alloc(&S.a1, W2 * 3));
+        SPLIT_TRY(alloc(&S.b2, W2 * 3));
+        SPLIT_TRY(alloc(&S.rho_pl, pl));
+        SPLIT_TRY(alloc(&S.w_pl, pl));
+        SPLIT_TRY(alloc(&S.w32, (size_t)2 * Dp * Dp));
+        SPLIT_TRY(alloc(&S.wt32, (size_t)2 * Dp * Dp));
+        SPLIT_TRY(alloc(&S.rho_df[0], (size_t)(D * D)));
+        SPLIT_TRY(alloc(&S.rho_df[1], (size_t)(D * D)));
+        SPLIT_TRY(alloc(&S.phase_df, (size_t)D));
+        QED_CUDA_TRY(cudaMemset(S.rho_pl, 0, pl * sizeof(__half)));
+        QED_CUDA_TRY(cudaMemset(S.w_pl, 0, pl * sizeof(__half)));
+        // GEMM1: Delta (hi, mid, lo) x rho (hi, lo): hi*hi + hi*lo + mid*hi + lo*hi
+        const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
+        // GEMM2: W (hi, lo) x Delta (hi, mid, lo): hi*hi + lo*hi + hi*mid
+        const int seg2[6] = {0, 0, 1, 0, 0, 1};
+        if (!tc_gemm_plan(S.g1, S.a1, 3, S.rho_pl, 2, (int)(2 * Dp), (int)Dp, (int)(2 * Dp), 4, seg1, S.num_sms))
             return QED_ECUDA;
-        if (!tc_gemm_plan(st->g2, sp.w_pl, sp.b2, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), st->num_sms))
+        if (!tc_gemm_plan(S.g2, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), 3, seg2, S.num_sms))
             return QED_ECUDA;
-        sp.partial_elems = (int64_t)std::max(st->g1.splits, st->g2.splits) * 2 * Dp * Dp;
-        if ((st_ = alloc((void **)&sp.partial, (size_t)sp.partial_elems * sizeof(float))) != QED_OK) return st_;
+        const size_t partial = (size_t)std::max(S.g1.splits, S.g2.splits) * 2 * Dp * Dp;
+        SPLIT_TRY(alloc(&S.partial, partial));
+        // per-row phases P_k as double-floats
+        std::vector<double2> ph((size_t)D);
+        QED_CUDA_TRY(cudaMemcpy(ph.data(), m->phase, (size_t)D * sizeof(double2), cudaMemcpyDeviceToHost));
+        std::vector<float4> pdf((size_t)D);
+        for (int64_t k = 0; k < D; ++k) {
+            const float rh = (float)ph[(size_t)k].x, ih = (float)ph[(size_t)k].y;
+            pdf[(size_t)k] = make_float4(rh, (float)(ph[(size_t)k].x - rh), ih, (float)(ph[(size_t)k].y - ih));
+        }
+        QED_CUDA_TRY(cudaMemcpy(S.phase_df, pdf.data(), (size_t)D * sizeof(float4), cudaMemcpyHostToDevice));
+        // dt/2 d_k and sqrt(dt) * coefficient as double-floats
+        auto split_f = [](double x) { const float h = (float)x; return make_float2(h, (float)(x - (double)h)); };
+        std::vector<double> anti((size_t)D);
+        QED_CUDA_TRY(cudaMemcpy(anti.data(), m->anti, (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float2> damp((size_t)D);
+        for (int64_t k = 0; k < D; ++k) damp[(size_t)k] = split_f(0.5 * m->dt * anti[(size_t)k]);
+        SPLIT_TRY(alloc(&S.damp_df, (size_t)D));
+        QED_CUDA_TRY(cudaMemcpy(S.damp_df, damp.data(), (size_t)D * sizeof(float2), cudaMemcpyHostToDevice));
+        std::vector<double> coef((size_t)m->n_in);
+        if (m->n_in > 0)
+            QED_CUDA_TRY(cudaMemcpy(coef.data(), m->in_coef, (size_t)m->n_in * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float2> cdf_((size_t)std::max<int64_t>(m->n_in, 1));
+        for (int64_t e = 0; e < m->n_in; ++e) cdf_[(size_t)e] = split_f(std::sqrt(m->dt) * coef[(size_t)e]);
+        SPLIT_TRY(alloc(&S.coef_df, cdf_.size()));
+        QED_CUDA_TRY(cudaMemcpy(S.coef_df, cdf_.data(), cdf_.size() * sizeof(float2), cudaMemcpyHostToDevice));
     }
-    // Delta into work1, its scale from the host copy, then the constant planes
+    SplitState &S = *m->sp;
+    // Delta into work1, its scales from a host copy, then the constant planes
     make_delta_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, m->U, m->phase, m->work1);
     count_launches(1);
     std::vector<double2> h((size_t)(D * D));
@@ -235,93 +547,80 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         maxrow = std::max(maxrow, row);
     }
     // largest scaled magnitude 2^14 (FP16 max 65504); |rho_kl| <= 1, |W_kl| <= max row sum of |Delta|
-    sp.scale_delta = pow2_scale(maxabs, 14);
-    sp.scale_rho = std::ldexp(1.0, 14);
-    sp.scale_w = pow2_scale(maxrow, 14);
-    static_planes_kernel<<<blocks_for((int64_t)W2, 256), 256, 0, s>>>(D, Dp, m->work1, sp.scale_delta,
-                                                                      (__half *)sp.a1, (__half *)sp.b2);
+    S.scale_delta = pow2_scale(maxabs, 14);
+    S.scale_rho = std::ldexp(1.0, 14);
+    S.scale_w = pow2_scale(maxrow, 14);
+    static_planes_kernel<<<blocks_for((int64_t)W2, 256), 256, 0, s>>>(D, Dp, m->work1, S.scale_delta, S.a1, S.b2);
     count_launches(1);
     QED_CUDA_TRY(cudaGetLastError());
     return QED_OK;
 }
 
-qed_status split_begin(qed_model *m, double2 *rho, cudaStream_t s) {
-    SplitPlanes &sp = m->sp;
+qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
+    SplitState &S = *m->sp;
     dim3 grid(blocks_for(m->D, 256), (unsigned)m->D);
-    rho_planes_kernel<<<grid, 256, 0, s>>>(m->D, sp.Dp, rho, sp.scale_rho, (__half *)sp.rho_pl);
+    import_kernel<<<grid, 256, 0, s>>>(m->D, S.Dp, rho, (float)S.scale_rho, S.rho_df[0], S.rho_pl);
     count_launches(1);
     QED_CUDA_TRY(cudaGetLastError());
     return QED_OK;
 }
 
-static void launch_w_reduce(qed_model *m, cudaStream_t s) {
-    SplitPlanes &sp = m->sp;
-    SplitState *st = state(m);
-    dim3 grid(blocks_for(sp.Dp, 256), (unsigned)(2 * sp.Dp));
-    w_reduce_kernel<<<grid, 256, 0, s>>>(sp.Dp, st->g1.splits, sp.partial, 1.0 / (sp.scale_delta * sp.scale_rho),
-                                         sp.scale_w, sp.w32, (__half *)sp.w_pl);
-    count_launches(1);
-}
-
-static void launch_form_v(qed_model *m, cudaStream_t s, const double2 *rho) {
-    SplitPlanes &sp = m->sp;
-    SplitState *st = state(m);
-    dim3 block(32, 8);
-    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
-    form_v_kernel<<<grid, block, 0, s>>>(m->D, sp.Dp, st->g2.splits, rho, sp.w32, sp.partial,
-                                         1.0 / (sp.scale_w * sp.scale_delta), m->phase, m->work2);
-    count_launches(1);
-}
-
-static void launch_dissipate(qed_model *m, cudaStream_t s, double2 *rho) {
-    SplitPlanes &sp = m->sp;
-    dim3 block(32, 8);
-    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
-    dissipate_split_kernel<<<grid, block, 0, s>>>(m->D, sp.Dp, m->work2, rho, m->anti, m->in_ptr, m->in_jump,
-                                                  m->in_src, m->in_coef, m->dt, sp.scale_rho, (__half *)sp.rho_pl);
-    count_launches(1);
-}
-
-void split_step(qed_model *m, double2 *rho, cudaStream_t s) {
-    SplitState *st = state(m);
-    tc_gemm_launch(st->g1, m->sp.partial, m->err, s);
+void split_step(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    tc_gemm_launch(S.g1, S.partial, m->err, s);
     launch_w_reduce(m, s);
-    tc_gemm_launch(st->g2, m->sp.partial, m->err, s);
-    launch_form_v(m, s, rho);
-    launch_dissipate(m, s, rho);
+    tc_gemm_launch(S.g2, S.partial, m->err, s);
+    launch_form(m, s);
+    launch_dissipate(m, s);
 }
 
-int split_step_timed(qed_model *m, double2 *rho, cudaStream_t s, std::string &label) {
-    SplitState *st = state(m);
+int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
+    SplitState &S = *m->sp;
     cudaEventRecord(m->ev[0], s);
-    tc_gemm_launch(st->g1, m->sp.partial, m->err, s);
+    tc_gemm_launch(S.g1, S.partial, m->err, s);
     cudaEventRecord(m->ev[1], s);
     launch_w_reduce(m, s);
     cudaEventRecord(m->ev[2], s);
-    tc_gemm_launch(st->g2, m->sp.partial, m->err, s);
+    tc_gemm_launch(S.g2, S.partial, m->err, s);
     cudaEventRecord(m->ev[3], s);
-    launch_form_v(m, s, rho);
+    launch_form(m, s);
     cudaEventRecord(m->ev[4], s);
-    launch_dissipate(m, s, rho);
+    launch_dissipate(m, s);
     cudaEventRecord(m->ev[5], s);
-    label = "gemm1_tc,w_reduce,gemm2_tc,form_v,dissipate_split";
+    label = "gemm1_tc,w_reduce,gemm2_tc,form_v,dissipate";
     return 5;
 }
 
-void split_renorm(qed_model *m, double2 *rho, cudaStream_t s) {
-    renormalise(s, m->D, rho, m->scalars, m->err);
-    split_begin(m, rho, s);
+void split_renorm(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    trace_df_kernel<<<1, 1024, 0, s>>>(m->D, S.rho_df[0], m->scalars, m->err);
+    dim3 block(32, 8);
+    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
+    symmetrise_df_kernel<<<grid, block, 0, s>>>(m->D, S.Dp, S.rho_df[0], m->scalars, m->err,
+                                                (float)S.scale_rho, S.rho_pl);
+    count_launches(2);
 }
 
-void split_sync_rho(qed_model *, double2 *, cudaStream_t) {}
+void split_observables(qed_model *m, const int32_t *ids, int32_t n_obs, double *out, cudaStream_t s) {
+    if (n_obs <= 0) return;
+    observables_df_kernel<<<n_obs, 256, 0, s>>>(m->D, m->sp->rho_df[0], m->obs_w, ids, out);
+    count_launches(1);
+}
+
+void split_end(qed_model *m, double2 *rho, cudaStream_t s) {
+    export_kernel<<<blocks_for(m->D * m->D, 256), 256, 0, s>>>(m->D, m->sp->rho_df[0], rho);
+    count_launches(1);
+}
 
 void split_release(qed_model *m) {
-    SplitPlanes &sp = m->sp;
-    void *ptrs[] = {sp.a1, sp.b2, sp.rho_pl, sp.w_pl, sp.w32, sp.partial};
+    if (!m->sp) return;
+    SplitState &S = *m->sp;
+    void *ptrs[] = {S.a1,        S.b2,        S.rho_pl,   S.w_pl,    S.w32,     S.wt32,
+                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    delete state(m);
-    sp.tmaps = nullptr;
+    delete m->sp;
+    m->sp = nullptr;
 }
 
 }  // namespace qed

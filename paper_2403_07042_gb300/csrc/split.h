@@ -1,6 +1,7 @@
 // Split-precision (increment form) step: U = P (I + Delta) with P = diag(exp(-i H_kk dt)),
 // so U rho U^+ = P (rho + W + W^+ + X) P^+ with W = Delta rho and X = W Delta^+; the two
-// products run on the tensor cores with FP16 hi/lo operands and FP32 accumulation.
+// products run on the tensor cores with FP16 pieces and FP32 accumulation, and the
+// master rho is kept as a double-float (two FP32 words) inside the library.
 #pragma once
 
 #include <string>
@@ -9,12 +10,13 @@
 
 namespace qed {
 
-qed_status split_prepare(qed_model *m, cudaStream_t s);      // Delta planes, buffers, TMA maps
-qed_status split_begin(qed_model *m, double2 *rho, cudaStream_t s);  // rho -> FP16 planes
-void split_step(qed_model *m, double2 *rho, cudaStream_t s);
-void split_renorm(qed_model *m, double2 *rho, cudaStream_t s);
-void split_sync_rho(qed_model *m, double2 *rho, cudaStream_t s);   // nothing pending after a step
-int split_step_timed(qed_model *m, double2 *rho, cudaStream_t s, std::string &label);
+qed_status split_prepare(qed_model *m, cudaStream_t s);                 // Delta planes, buffers, TMA maps
+qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s);  // caller rho -> internal state
+void split_step(qed_model *m, cudaStream_t s);
+void split_renorm(qed_model *m, cudaStream_t s);
+void split_observables(qed_model *m, const int32_t *ids, int32_t n_obs, double *out, cudaStream_t s);
+void split_end(qed_model *m, double2 *rho, cudaStream_t s);              // internal state -> caller rho
+int split_step_timed(qed_model *m, cudaStream_t s, std::string &label);
 void split_release(qed_model *m);
 
 }  // namespace qed

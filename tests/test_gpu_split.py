@@ -39,6 +39,15 @@ def _planes(rng, rows, K, scale):
     return np.stack([hi, lo])
 
 
+def _planes3(rng, rows, K, scale):
+    x = rng.standard_normal((rows, K)) * scale
+    hi = x.astype(np.float16)
+    r = x - hi.astype(np.float64)
+    mid = r.astype(np.float16)
+    lo = (r - mid.astype(np.float64)).astype(np.float16)
+    return np.stack([hi, mid, lo])
+
+
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (256, 384, 512, 1), (256, 128, 1024, 3),
                                           (384, 256, 256, 4)])
 def test_tc_gemm_three_term_product(M, N, K, splits):
@@ -55,8 +64,26 @@ def test_tc_gemm_three_term_product(M, N, K, splits):
     got = out.sum(axis=0)
     assert out.shape == (splits, M, N)
     assert np.all(np.abs(got - want) <= bound)
-    # the three terms are really there: dropping A_lo or B_lo is detectable
-    assert np.abs(got - Ah @ Bh.T).max() > 10 * bound.max()
+    print(f"tc_gemm {M}x{N}x{K}/{splits}: max err / (sum|ab| 2^-24) = "
+          f"{(np.abs(got - want) / (bound / (6 * K))).max():.1f}")
+    # the lo terms are really there: the result is far closer to the three-term product
+    # than to hi*hi alone
+    assert np.abs(got - want).max() < 0.1 * np.abs(want - Ah @ Bh.T).max()
+
+
+def test_tc_gemm_four_segments_three_planes():
+    """The step's GEMM1 form: A in three pieces, B in two, four plane pairs."""
+    rng = np.random.default_rng(7)
+    M, N, K = 256, 128, 256
+    A = _planes3(rng, M, K, 1.0)
+    B = _planes(rng, N, K, 1.0)
+    seg = ((0, 0), (0, 1), (1, 0), (2, 0))
+    out = qed.tc_gemm(_cuda(A), _cuda(B), segments=seg, splits=2).cpu().numpy().astype(np.float64).sum(0)
+    Af = A.astype(np.float64)
+    Bf = B.astype(np.float64)
+    want = sum(Af[p] @ Bf[q].T for p, q in seg)
+    bound = 4 * K * 2.0 ** -23 * (np.abs(Af).sum(0) @ np.abs(Bf).sum(0).T)
+    assert np.all(np.abs(out - want) <= bound)
 
 
 def test_tc_gemm_rejects_bad_shapes():
@@ -64,6 +91,9 @@ def test_tc_gemm_rejects_bad_shapes():
     b = torch.zeros((2, 128, 64), dtype=torch.float16, device="cuda")
     with pytest.raises(qed.QedError):
         qed.tc_gemm(a, b)
+    b2 = torch.zeros((2, 128, 64), dtype=torch.float16, device="cuda")
+    with pytest.raises(qed.QedError):
+        qed.tc_gemm(b2, b2, segments=((0, 2),))
 
 
 def _evolve(model, n_steps, precision, rho0=None, U=None, record_every=0, obs=None):
