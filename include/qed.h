@@ -208,6 +208,25 @@ qed_status qed_tc_gemm(const void *a_planes, int32_t planes_a, const void *b_pla
                        int32_t M, int32_t N, int32_t K, int32_t n_seg, const int32_t *seg_pairs,
                        int32_t splits, float *out, qed_stream stream);
 
+/*
+ * The same product as qed_tc_gemm, for callers that cannot allocate device memory (code
+ * that runs inside another framework's fixed memory pool, or whose allocations are all
+ * made up front): it calls no cudaMalloc, cudaFree or allocating library routine.  The
+ * split-K partial sums live in a file-scope device array of 4 Mi floats (16 MiB) that
+ * every GPU loading the library holds until exit, plus a device error word; out is
+ * device FP32 [M][N], the summed product (not the partials).  The paper has no
+ * counterpart: this is a deployment variant of the library's own GEMM.
+ *   - EINVAL when splits * M * N exceeds 4 Mi floats, or on the shape rules of qed_tc_gemm.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's partials; calls whose work
+ *     overlaps on the GPU (two streams, two host threads) race on it.
+ * Synchronises `stream` to report ETIMEOUT from a bounded device wait.
+ */
+qed_status qed_tc_gemm_static(const void *a_planes, int32_t planes_a, const void *b_planes, int32_t planes_b,
+                              int32_t M, int32_t N, int32_t K, int32_t n_seg, const int32_t *seg_pairs,
+                              int32_t splits, float *out, qed_stream stream);
+
 /* Total number of kernels this library has launched in this process (all models). */
 qed_status qed_launch_count(int64_t *count);
 

@@ -83,6 +83,7 @@ def lib():
         "qed_profile": [vp, vp, i64, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_launch_count": [ctypes.POINTER(i64)],
         "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
+        "qed_tc_gemm_static": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -199,6 +200,24 @@ def tc_gemm(a_planes, b_planes, segments=((0, 0), (0, 1), (1, 0)), splits=1, str
                              ctypes.c_void_p(b_planes.data_ptr()), b_planes.shape[0], M, N, K, len(segments),
                              seg.ctypes.data_as(_c_int32_p), splits, ctypes.c_void_p(out.data_ptr()),
                              _stream_handle(stream)), "qed_tc_gemm")
+    return out
+
+
+def tc_gemm_static(a_planes, b_planes, segments=((0, 0), (0, 1), (1, 0)), splits=1, out=None, stream=None):
+    """The summed product [M, N] (FP32) of tc_gemm, computed without any device
+    allocation inside the library: its split-K partials use the library's static scratch
+    (splits * M * N <= 4 Mi floats).  `out` may be a caller-owned CUDA float32 tensor."""
+    import torch
+    M, K = a_planes.shape[1], a_planes.shape[2]
+    N = b_planes.shape[1]
+    seg = _arr([x for pq in segments for x in pq], np.int32)
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=a_planes.device)
+    _check(lib().qed_tc_gemm_static(ctypes.c_void_p(a_planes.data_ptr()), a_planes.shape[0],
+                                    ctypes.c_void_p(b_planes.data_ptr()), b_planes.shape[0], M, N, K,
+                                    len(segments), seg.ctypes.data_as(_c_int32_p), splits,
+                                    ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "qed_tc_gemm_static")
     return out
 
 
