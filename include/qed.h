@@ -167,6 +167,24 @@ qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_off
                       int32_t record_every, int32_t n_obs, const int32_t *obs_ids,
                       double *records, qed_stream stream);
 
+/*
+ * Gradients of the loss L = tr(diag(obs_diag) rho_N) after n_steps steps from rho0 (device
+ * complex128 D x D, not modified), by the discrete adjoint of the step qed_evolve takes
+ * (Eq. 2 and Eq. 3, unitary part then one Euler step of the Lindblad term):
+ *   lambda_N = diag(obs_diag);  kappa = J^+(lambda_{n+1});  lambda_n = U^+ kappa U;
+ *   dL/dgamma_j = dt sum_n tr(lambda_{n+1} D_j(V_n));
+ *   dL/dtheta   = 2 dt Im tr(G dH/dtheta),  G = L_exp(-i dt H, sum_n rho_n U^+ kappa_{n+1}),
+ * the Frechet derivative taken once as a block of exp([[X, M], [0, X]]).  rho is
+ * checkpointed every `checkpoint_every` steps and recomputed in between.  Outputs are
+ * device FP64: *loss; grad_g[total atoms], grad_zeta[n_bonds], grad_gamma[n_jumps] in the
+ * order of the spec (each may be NULL only if its count is 0).  The FP64 kernels carry
+ * the adjoint for every model precision.  Allocates its work space (checkpoints, one
+ * segment of rho_n and V_n, the 2D x 2D block) per call; synchronises `stream`.
+ */
+qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t checkpoint_every,
+                       const double *obs_diag, double *loss, double *grad_g, double *grad_zeta,
+                       double *grad_gamma, qed_stream stream);
+
 /* Observables of one rho (device) into out (device FP64 [n_obs]). */
 qed_status qed_observables(const qed_model *m, const void *rho, int32_t n_obs,
                            const int32_t *obs_ids, double *out, qed_stream stream);

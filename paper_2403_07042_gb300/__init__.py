@@ -82,6 +82,7 @@ def lib():
         "qed_get_U": [vp, vp, vp],
         "qed_profile": [vp, vp, i64, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_launch_count": [ctypes.POINTER(i64)],
+        "qed_adjoint": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
         "qed_tc_gemm_static": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
     }
@@ -319,6 +320,24 @@ class Model:
                                      _stream_handle(stream)), "qed_observables")
         return out
 
+    def adjoint(self, rho0, n_steps, obs_diag, checkpoint_every=50, stream=None):
+        """(loss, grad_g, grad_zeta, grad_gamma) of tr(diag(obs_diag) rho_N) as CUDA FP64
+        tensors; rho0 a CUDA complex128 D x D tensor, obs_diag a CUDA FP64 vector."""
+        import torch
+        _check_rho(rho0, self.dim)
+        m = self.spec_dict
+        dev = rho0.device
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        gg = torch.zeros(max(len(m["g"]), 1), dtype=torch.float64, device=dev)
+        gz = torch.zeros(max(len(m["zeta"]), 1), dtype=torch.float64, device=dev)
+        gj = torch.zeros(max(len(m["jumps"]), 1), dtype=torch.float64, device=dev)
+        o = obs_diag.to(device=dev, dtype=torch.float64).contiguous()
+        _check(lib().qed_adjoint(self._h, ctypes.c_void_p(rho0.data_ptr()), int(n_steps), int(checkpoint_every),
+                                 ctypes.c_void_p(o.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                 ctypes.c_void_p(gg.data_ptr()), ctypes.c_void_p(gz.data_ptr()),
+                                 ctypes.c_void_p(gj.data_ptr()), _stream_handle(stream)), "qed_adjoint")
+        return loss[0], gg[: len(m["g"])], gz[: len(m["zeta"])], gj[: len(m["jumps"])]
+
     def sync(self, stream=None):
         _check(lib().qed_sync_status(self._h, _stream_handle(stream)), "qed_sync_status")
 
@@ -350,3 +369,38 @@ def _check_rho(rho, dim):
         raise TypeError("expected a CUDA complex128 tensor")
     if tuple(rho.shape) != (dim, dim) or not rho.is_contiguous():
         raise ValueError(f"expected a contiguous {dim} x {dim} tensor")
+
+
+def _autograd_function():
+    import torch
+
+    class QMELoss(torch.autograd.Function):
+        """L = tr(diag(obs) rho_N) as a differentiable function of the couplings g, the
+        hoppings zeta and the rates gamma (CPU or CUDA FP64 tensors).  The forward builds
+        the model with these parameters and runs qed_adjoint, whose gradients the backward
+        returns (scaled by the incoming gradient)."""
+
+        @staticmethod
+        def forward(ctx, g, zeta, gamma, model, rho0, n_steps, obs_diag, checkpoint_every, precision):
+            m = dict(model)
+            m["g"] = [float(x) for x in g.detach().cpu()]
+            m["zeta"] = [float(x) for x in zeta.detach().cpu()]
+            m["jumps"] = [(k, s_, float(x)) for (k, s_, _), x in zip(model["jumps"], gamma.detach().cpu())]
+            gm = Model(m, precision=precision)
+            loss, gg, gz, gj = gm.adjoint(rho0, n_steps, obs_diag, checkpoint_every)
+            ctx.save_for_backward(gg.to(g.device), gz.to(zeta.device), gj.to(gamma.device))
+            gm.close()
+            return loss.to(g.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gg, gz, gj = ctx.saved_tensors
+            return grad_out * gg, grad_out * gz, grad_out * gj, None, None, None, None, None, None
+
+    return QMELoss
+
+
+def qme_loss(g, zeta, gamma, model, rho0, n_steps, obs_diag, checkpoint_every=50, precision="fp64"):
+    """Differentiable tr(diag(obs_diag) rho_N) (see QMELoss)."""
+    return _autograd_function().apply(g, zeta, gamma, model, rho0, n_steps, obs_diag, checkpoint_every,
+                                      precision)

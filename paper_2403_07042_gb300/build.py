@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqed.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["builder.cpp", "capi.cu", "kernels_f64.cu", "split.cu", "gemm_tc.cu", "gemm_static.cu"]
+SOURCES = ["builder.cpp", "capi.cu", "kernels_f64.cu", "split.cu", "gemm_tc.cu", "gemm_static.cu", "expm.cu", "adjoint.cu"]
 
 
 def nvcc():

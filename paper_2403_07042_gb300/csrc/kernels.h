@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "qed.h"
+
 namespace qed {
 
 // Number of kernels this library has launched (all launchers add to it).
@@ -16,6 +18,10 @@ int64_t launches();
 void zgemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A,
            int64_t lda, const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C,
            int64_t ldc);
+
+// C = alpha * op(A) * op(B) + beta * C with op(A) = A (M x K) or A^+ (A is K x M).
+void zgemm_ex(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A, int64_t lda,
+              bool conj_a, const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C, int64_t ldc);
 
 // Y = c0 A + c1 B + c2 C + c3 I + c4 Y (real coefficients; any of A, B, C may be null).
 void zlincomb(cudaStream_t s, int64_t D, double c0, const double2 *A, double c1, const double2 *B,
@@ -42,6 +48,12 @@ void dissipate_f64(cudaStream_t s, int64_t D, const double2 *V, double2 *rho, co
 // out[o] = rho_kk (id < D), or sum_k w[id-D][k] rho_kk; deterministic block reduction.
 void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights,
                  const int32_t *ids, int32_t n_obs, double *out);
+
+// U = exp(-i dt H) (H Hermitian, device) and R = exp(X) (general X with 1-norm xnorm):
+// Pade-13 scaling and squaring; allocate their own work space; synchronise `s`.
+qed_status propagator(cudaStream_t s, int64_t D, double dt, const double2 *H, double h_norm1, double2 *U,
+                      uint32_t *err);
+qed_status expm_pade13(cudaStream_t s, int64_t D, const double2 *X, double xnorm, double2 *R, uint32_t *err);
 
 // rho <- (rho + rho^+) / (2 tr rho); flags non-finite traces in *err.
 void renormalise(cudaStream_t s, int64_t D, double2 *rho, double *scratch, uint32_t *err);

@@ -24,7 +24,7 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // c
 constexpr int TM = 32, TN = 32, TK = 16;
 
 // 64 threads; thread (ty, tx) in 8 x 8 owns rows ty + 8i and columns tx + 8j.
-template <bool CONJ_B>
+template <bool CONJ_A, bool CONJ_B>
 __global__ void __launch_bounds__(64) zgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                    const double2 *__restrict__ A, int64_t lda,
                                                    const double2 *__restrict__ B, int64_t ldb,
@@ -41,11 +41,21 @@ __global__ void __launch_bounds__(64) zgemm_kernel(int64_t M, int64_t N, int64_t
         for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
     for (int64_t k0 = 0; k0 < K; k0 += TK) {
+        if (!CONJ_A) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {  // A tile: 32 rows x 16 k, coalesced along k
-            int mm = (t >> 4) + 4 * r, kk = t & 15;
-            int64_t gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? A[gm * lda + gk] : make_double2(0.0, 0.0);
+            for (int r = 0; r < 8; ++r) {  // A tile: 32 rows x 16 k, coalesced along k
+                int mm = (t >> 4) + 4 * r, kk = t & 15;
+                int64_t gm = m0 + mm, gk = k0 + kk;
+                As[kk][mm] = (gm < M && gk < K) ? A[gm * lda + gk] : make_double2(0.0, 0.0);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {  // op(A)[m][k] = conj(A[k][m]), coalesced along m
+                int mm = t & 31, kk = (t >> 5) + 2 * r;
+                int64_t gm = m0 + mm, gk = k0 + kk;
+                double2 v = (gm < M && gk < K) ? A[gk * lda + gm] : make_double2(0.0, 0.0);
+                As[kk][mm] = make_double2(v.x, -v.y);
+            }
         }
         if (!CONJ_B) {
 #pragma unroll
@@ -282,14 +292,26 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 
 }  // namespace
 
-void zgemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A, int64_t lda,
-           const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C, int64_t ldc) {
+void zgemm_ex(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A, int64_t lda,
+              bool conj_a, const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C, int64_t ldc) {
     count_launches(1);
     dim3 grid(blocks_for(N, TN), blocks_for(M, TM));
-    if (conj_b)
-        zgemm_kernel<true><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else
-        zgemm_kernel<false><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (conj_a) {
+        if (conj_b)
+            zgemm_kernel<true, true><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        else
+            zgemm_kernel<true, false><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    } else {
+        if (conj_b)
+            zgemm_kernel<false, true><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        else
+            zgemm_kernel<false, false><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    }
+}
+
+void zgemm(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, const double2 *A, int64_t lda,
+           const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C, int64_t ldc) {
+    zgemm_ex(s, M, N, K, alpha, A, lda, false, B, ldb, conj_b, beta, C, ldc);
 }
 
 void zlincomb(cudaStream_t s, int64_t D, double c0, const double2 *A, double c1, const double2 *B, double c2,

@@ -10,6 +10,8 @@
 #include "builder.h"
 #include "qed.h"
 
+struct qed_model;
+
 namespace qed {
 
 void set_error(const std::string &msg);
@@ -32,6 +34,9 @@ enum : uint32_t {
 
 // State of the split-precision (increment form) path; defined in split.cu.
 struct SplitState;
+// Tables of the adjoint (gradients); defined in adjoint.cu.
+struct AdjointState;
+void adjoint_release(qed_model *m);
 
 }  // namespace qed
 
@@ -65,6 +70,7 @@ struct qed_model {
     uint32_t *err_host = nullptr;     // pinned mirror
 
     qed::SplitState *sp = nullptr;
+    qed::AdjointState *adj = nullptr;
     cudaEvent_t ev[16] = {};
 
     // step loop as CUDA graphs: graph[0] runs 1 step, graph[1] runs kGraphSteps steps

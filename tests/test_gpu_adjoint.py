@@ -1,0 +1,135 @@
+"""GPU adjoint gradients (qed_adjoint) against the oracle's discrete adjoint, central
+finite differences of the GPU forward, and the closed-form Rabi gradient."""
+import numpy as np
+import pytest
+
+import oracle
+import qed_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+qed = pytest.importorskip("paper_2403_07042_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_07042_gb300 import build
+    build.build()
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _gpu_adjoint(m, steps, w, k, rho0=None, b=None):
+    b = b or oracle.enumerate_basis(m)
+    gm = qed.Model(m)
+    rho0 = oracle.initial_density(m, b) if rho0 is None else rho0
+    loss, gg, gz, gj = gm.adjoint(_cuda(rho0), steps, _cuda(w), checkpoint_every=k)
+    return float(loss), gg.cpu().numpy(), gz.cpu().numpy(), gj.cpu().numpy()
+
+
+def _close(a, b, rtol):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    scale = max(np.abs(b).max(), 1e-30)
+    return np.abs(a - b).max() <= rtol * scale
+
+
+@pytest.mark.parametrize("k", [7, 60, 1])
+def test_adjoint_matches_oracle_lattice(k):
+    m = W.lattice(3, 3, seed=4, gamma=0.02, dt=0.1, n_steps=60, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    ref = oracle.adjoint_gradients(m, w, basis=b)
+    got = _gpu_adjoint(m, 60, w, k, b=b)
+    assert abs(got[0] - ref[0]) <= 1e-12
+    for x, y in zip(got[1:], ref[1:]):
+        assert _close(x, y, 1e-9)
+
+
+def test_adjoint_matches_oracle_cavities_and_dephasing():
+    """Photon-loss jumps on a full product basis plus extra-digit dephasing, random mixed
+    initial state, ragged checkpoint segments."""
+    m = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+             zeta=[0.006], dt=0.1)
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=11)
+    w = np.random.default_rng(2).uniform(0, 1, b.dim)
+    ref = oracle.adjoint_gradients(m, w, n_steps=45, rho0=rho0, basis=b)
+    got = _gpu_adjoint(m, 45, w, 10, rho0=rho0, b=b)
+    assert abs(got[0] - ref[0]) <= 1e-12
+    for x, y in zip(got[1:], ref[1:]):
+        assert _close(x, y, 1e-9)
+
+
+def test_rabi_gradient_closed_form():
+    g, dt, steps, n = 0.05, 0.1, 300, 1
+    m = W.jc_single(n_max=3, g=g, dt=dt, n_steps=steps, init_photons=n)
+    b = oracle.enumerate_basis(m)
+    w = (b.digits[:, b.atom_digit(0)] == 1).astype(float)
+    loss, gg, _, _ = _gpu_adjoint(m, steps, w, 64, b=b)
+    t, s = dt * steps, np.sqrt(n + 1)
+    assert abs(loss - np.cos(g * s * t) ** 2) <= 1e-12
+    assert abs(gg[0] - (-s * t * np.sin(2 * g * s * t))) <= 1e-9
+
+
+def test_adjoint_against_gpu_finite_differences():
+    """Fourth-order central differences (h = 1e-3) of the GPU FP64 forward."""
+    m = W.lattice(4, 4, seed=9, gamma=0.01, dt=0.1, n_steps=80, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    loss, gg, gz, gj = _gpu_adjoint(m, 80, w, 16, b=b)
+    rho0 = oracle.initial_density(m, b)
+
+    def forward(mm):
+        gm = qed.Model(mm)
+        rho = _cuda(rho0)
+        gm.evolve(rho, 80)
+        gm.sync()
+        return float(np.sum(w * np.real(np.diag(rho.cpu().numpy()))))
+
+    h = 1e-3
+    for name, i, grad in (("g", 0, gg[0]), ("g", 5, gg[5]), ("zeta", 1, gz[1]), ("zeta", 3, gz[3])):
+        def f(d):
+            mm = dict(m)
+            arr = list(mm[name])
+            arr[i] += d
+            mm[name] = arr
+            return forward(mm)
+        fd = (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+        assert abs(grad - fd) <= 1e-6 * abs(fd) + 1e-10, (name, i, grad, fd)
+    j = 0
+
+    def fj(d):
+        jumps = [(kk, s, gmm + (d if q == j else 0.0)) for q, (kk, s, gmm) in enumerate(m["jumps"])]
+        return forward(dict(m, jumps=jumps))
+    fd = (-fj(2 * h) + 8 * fj(h) - 8 * fj(-h) + fj(-2 * h)) / (12 * h)
+    assert abs(gj[j] - fd) <= 1e-6 * abs(fd) + 1e-10
+
+
+def test_autograd_function():
+    m = W.lattice(3, 3, seed=4, gamma=0.02, dt=0.1, n_steps=30, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    ref = oracle.adjoint_gradients(m, w, n_steps=30, basis=b)
+    g = torch.tensor(m["g"], dtype=torch.float64, requires_grad=True)
+    z = torch.tensor(m["zeta"], dtype=torch.float64, requires_grad=True)
+    gam = torch.tensor([x[2] for x in m["jumps"]], dtype=torch.float64, requires_grad=True)
+    loss = qed.qme_loss(g, z, gam, m, _cuda(oracle.initial_density(m, b)), 30, _cuda(w), 8)
+    (2.0 * loss).backward()
+    assert abs(float(loss.detach()) - ref[0]) <= 1e-12
+    assert _close(g.grad.numpy(), 2 * ref[1], 1e-9)
+    assert _close(z.grad.numpy(), 2 * ref[2], 1e-9)
+    assert _close(gam.grad.numpy(), 2 * ref[3], 1e-9)
+
+
+def test_adjoint_argument_errors():
+    m = W.jch_two_cavities()
+    gm = qed.Model(m)
+    rho = torch.zeros((36, 36), dtype=torch.complex128, device="cuda")
+    with pytest.raises(qed.QedError):
+        gm.adjoint(rho, 10, torch.zeros(36, dtype=torch.float64, device="cuda"), checkpoint_every=0)

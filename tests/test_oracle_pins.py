@@ -180,6 +180,16 @@ def test_tight_binding_closed_form():
     assert np.abs(rho[np.ix_(idx, idx)] - want).max() < 1e-12
 
 
+def test_lattice_closed_form_with_atoms():
+    """Uniform-g lattice, one excitation: each open-boundary hopping mode is a 2 x 2 JC
+    block, giving the state in closed form (tests/closed_forms.py)."""
+    from closed_forms import lattice_single_excitation_state
+    m = W.lattice(5, 4, g=0.02, zeta=0.03, gamma=0.0, dt=0.1, n_steps=150, start=(1, 2))
+    rho = oracle.evolve(m, return_records=False)
+    psi = lattice_single_excitation_state(5, 4, 1.0, 0.02, 0.03, 15.0, (1, 2))
+    assert np.abs(rho - np.outer(psi, psi.conj())).max() < 1e-12
+
+
 def test_discrete_photon_decay():
     """H = omega a^+a, A = a: <n>_k = (1 - gamma dt)^k <n>_0 exactly for the scheme,
     because a^+ (a^+ a) a = n(n - 1) and the anticommutator removes 2n^2 gamma dt / 2."""
