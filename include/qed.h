@@ -185,6 +185,21 @@ qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t 
                        const double *obs_diag, double *loss, double *grad_g, double *grad_zeta,
                        double *grad_gamma, qed_stream stream);
 
+/*
+ * Evolve n independent models together, each by n_steps steps of qed_evolve's step:
+ * rhos[i] (device complex128 D_i x D_i, in/out) belongs to ms[i].  For split-precision
+ * models every phase of a step is one grouped launch over all instances (the tcgen05
+ * GEMM's work items are the 128 x 128 tiles of every instance, largest first; the element
+ * kernels' blocks tile every instance), and the step loop is captured in CUDA graphs.
+ * FP64 models run one after another.  All models must share one precision and appear
+ * once.  records (host array of n device pointers, or NULL): records[i] (device FP64, or
+ * NULL) receives the populations rho_kk of instance i, row-major [n_rec x D_i], at steps
+ * 0, r, 2r, ... <= n_steps (r = record_every).  Each model's renormalisation setting
+ * applies.  Synchronises `stream` before returning (it frees the batch's tables).
+ */
+qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos, int64_t n_steps,
+                              int32_t record_every, double *const *records, qed_stream stream);
+
 /* Observables of one rho (device) into out (device FP64 [n_obs]). */
 qed_status qed_observables(const qed_model *m, const void *rho, int32_t n_obs,
                            const int32_t *obs_ids, double *out, qed_stream stream);

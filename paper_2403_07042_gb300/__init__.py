@@ -83,6 +83,7 @@ def lib():
         "qed_profile": [vp, vp, i64, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_launch_count": [ctypes.POINTER(i64)],
         "qed_adjoint": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
+        "qed_evolve_batched": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, i32, ctypes.POINTER(vp), vp],
         "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
         "qed_tc_gemm_static": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
     }
@@ -361,6 +362,29 @@ class Model:
                "qed_profile")
         labels = [x for x in names.value.decode().split(",") if x]
         return dict(zip(labels, ms[: len(labels)].tolist()))
+
+
+def evolve_batched(models, rhos, n_steps, record_every=0, records=None, stream=None):
+    """Advance every rhos[i] (CUDA complex128, in place) by n_steps steps of models[i]
+    together (qed_evolve_batched).  With record_every > 0 returns, per instance, a CUDA
+    FP64 tensor [n_rec, D_i] of populations (or fills the given `records` tensors)."""
+    import torch
+    n = len(models)
+    if n != len(rhos):
+        raise ValueError("one rho per model")
+    for m, r in zip(models, rhos):
+        _check_rho(r, m.dim)
+    if record_every > 0 and records is None:
+        nrec = n_steps // record_every + 1
+        records = [torch.zeros((nrec, m.dim), dtype=torch.float64, device=r.device) for m, r in zip(models, rhos)]
+    H = (ctypes.c_void_p * n)(*[m._h.value for m in models])
+    R = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    rec = None
+    if records is not None:
+        rec = (ctypes.c_void_p * n)(*[x.data_ptr() for x in records])
+    _check(lib().qed_evolve_batched(n, H, R, int(n_steps), int(record_every), rec, _stream_handle(stream)),
+           "qed_evolve_batched")
+    return records
 
 
 def _check_rho(rho, dim):

@@ -424,6 +424,100 @@ qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_o
     return QED_OK;
 }
 
+qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos, int64_t n_steps,
+                              int32_t record_every, double *const *records, qed_stream stream) {
+    if (n <= 0 || !ms || !rhos) return einval("qed_evolve_batched: need n > 0 models and rho pointers");
+    if (n_steps < 0) return einval("qed_evolve_batched: negative step count");
+    if (records && record_every <= 0) return einval("qed_evolve_batched: records need record_every > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool split = ms[0] && ms[0]->prec != QED_FP64;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ms[i] || !rhos[i]) return einval("qed_evolve_batched: NULL model or rho");
+        if ((ms[i]->prec != QED_FP64) != split) return einval("qed_evolve_batched: mixed precisions in one batch");
+        for (int32_t j = 0; j < i; ++j)
+            if (ms[j] == ms[i]) return einval("qed_evolve_batched: a model appears twice");
+    }
+    if (!split) {
+        // FP64 instances run one after another (each with its own step graphs)
+        for (int32_t i = 0; i < n; ++i) {
+            qed_model *m = ms[i];
+            std::vector<int32_t> ids;
+            if (records && records[i])
+                for (int64_t k = 0; k < m->D; ++k) ids.push_back((int32_t)k);
+            QED_TRY(qed_evolve(m, rhos[i], n_steps, 0, record_every, (int32_t)ids.size(), ids.data(),
+                               records ? records[i] : nullptr, stream));
+        }
+        return QED_OK;
+    }
+    for (int32_t i = 0; i < n; ++i) QED_TRY(split_begin(ms[i], (const double2 *)rhos[i], s));
+    Batch *b = nullptr;
+    QED_TRY(split_batch_create(ms, n, &b));
+    // the step loop as graphs of 1 and kGraphSteps grouped steps
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g[2] = {nullptr, nullptr};
+    int64_t gk[2] = {0, 0};
+    bool graphs = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+    const int64_t counts[2] = {1, kGraphSteps};
+    for (int q = 0; q < 2 && graphs; ++q) {
+        const int64_t before = launches();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { graphs = false; break; }
+        for (int64_t k = 0; k < counts[q]; ++k) split_batch_step(b, ms[0]->err, cap);
+        const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        gk[q] = launches() - before;
+        count_launches(-gk[q]);
+        if (e != cudaSuccess || !graph || cudaGraphInstantiate(&g[q], graph, 0) != cudaSuccess) graphs = false;
+        if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+    auto run = [&](int64_t k) -> qed_status {
+        if (!graphs) {
+            for (; k > 0; --k) split_batch_step(b, ms[0]->err, s);
+            return QED_OK;
+        }
+        for (; k >= kGraphSteps; k -= kGraphSteps) {
+            QED_CUDA_TRY(cudaGraphLaunch(g[1], s));
+            count_launches(gk[1]);
+        }
+        for (; k > 0; --k) {
+            QED_CUDA_TRY(cudaGraphLaunch(g[0], s));
+            count_launches(gk[0]);
+        }
+        return QED_OK;
+    };
+    int64_t row = 0;
+    auto record = [&](int64_t p) {
+        if (records && p % record_every == 0) {
+            for (int32_t i = 0; i < n; ++i)
+                if (records[i]) split_populations(ms[i], records[i] + row * ms[i]->D, s);
+            ++row;
+        }
+    };
+    qed_status st = QED_OK;
+    record(0);
+    for (int64_t i = 0; i < n_steps && st == QED_OK;) {
+        int64_t p = n_steps;
+        if (records) p = std::min(p, next_multiple_after(0, i, record_every));
+        for (int32_t q = 0; q < n; ++q)
+            if (ms[q]->renorm_every > 0) p = std::min(p, next_multiple_after(0, i, ms[q]->renorm_every));
+        st = run(p - i);
+        i = p;
+        for (int32_t q = 0; q < n; ++q)
+            if (ms[q]->renorm_every > 0 && p % ms[q]->renorm_every == 0) split_renorm(ms[q], s);
+        record(p);
+    }
+    for (int32_t i = 0; i < n; ++i) split_end(ms[i], (double2 *)rhos[i], s);
+    // the graphs and the batch tables are released once this call's work has finished
+    cudaStreamSynchronize(s);
+    for (auto &x : g)
+        if (x) cudaGraphExecDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+    split_batch_destroy(b);
+    if (st != QED_OK) return st;
+    QED_CUDA_TRY(cudaGetLastError());
+    return QED_OK;
+}
+
 qed_status qed_observables(const qed_model *m_c, const void *rho, int32_t n_obs, const int32_t *obs_ids, double *out,
                            qed_stream stream) {
     qed_model *m = const_cast<qed_model *>(m_c);

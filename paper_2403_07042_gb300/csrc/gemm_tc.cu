@@ -130,8 +130,11 @@ struct Params {
     uint32_t *err;
 };
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                         const __grid_constant__ CUtensorMap tmB, Params p) {
+// One 128 x 128 output tile of one split-K slice (the body shared by the single and the
+// grouped kernel).  tmA / tmB are generic addresses of tensor maps in parameter or global
+// memory.
+__device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const Params &p,
+                                          int tile_m, int tile_n, int split) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
@@ -143,7 +146,6 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     volatile int *consumed = abort_flag + 2;  // stage loads the MMA issuer has waited for
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_n = blockIdx.x, tile_m = blockIdx.y, split = blockIdx.z;
     const int kb0 = split * p.kb_per_split;
     const int nkb = min(p.kb_per_split, p.kb_total - kb0);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages),
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         *issued = 0;
         *consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmB) : "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -188,8 +190,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             const int seg = kb / p.kb_per_seg, kk = kb % p.kb_per_seg;
             const uint32_t bar = full0 + 8 * s;
             mbar_expect_tx(bar, kStageA + kStageB);
-            tma_load_3d(smem_u32(sA + s * kStageA), &tmA, kk * kTcBK, tile_m * kTcBM, p.seg_a[seg], bar);
-            tma_load_3d(smem_u32(sB + s * kStageB), &tmB, kk * kTcBK, tile_n * kTcBN, p.seg_b[seg], bar);
+            tma_load_3d(smem_u32(sA + s * kStageA), tmA, kk * kTcBK, tile_m * kTcBM, p.seg_a[seg], bar);
+            tma_load_3d(smem_u32(sB + s * kStageB), tmB, kk * kTcBK, tile_n * kTcBN, p.seg_b[seg], bar);
             *issued = i + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -246,6 +248,34 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN) : "memory");
     }
+}
+
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB, Params p) {
+    gemm_tile(&tmA, &tmB, p, blockIdx.y, blockIdx.x, blockIdx.z);
+}
+
+// Grouped launch: CTA b computes work item items[b] of job items[b].job (one instance of
+// a batch), with that job's tensor maps read from global memory.
+__global__ void __launch_bounds__(128, 1) tc_gemm_grouped_kernel(const GemmItem *__restrict__ items,
+                                                                 const GemmJob *__restrict__ jobs, TcSegs segs,
+                                                                 uint32_t *err) {
+    const GemmItem it = items[blockIdx.x];
+    const GemmJob jb = jobs[it.job];
+    Params p;
+    p.M = jb.M;
+    p.N = jb.N;
+    p.kb_per_seg = jb.kb_per_seg;
+    p.kb_total = segs.nseg * jb.kb_per_seg;
+    p.kb_per_split = jb.kb_per_split;
+#pragma unroll
+    for (int q = 0; q < kTcMaxSeg; ++q) {
+        p.seg_a[q] = segs.a[q];
+        p.seg_b[q] = segs.b[q];
+    }
+    p.out = jb.out;
+    p.err = err;
+    gemm_tile(jb.map_a, jb.map_b, p, it.tile_m, it.tile_n, it.split);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -338,6 +368,26 @@ bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_p
         }
         attr_set = true;
     }
+    return true;
+}
+
+void tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs,
+                            uint32_t *err, cudaStream_t s) {
+    if (n_items <= 0) return;
+    count_launches(1);
+    tc_gemm_grouped_kernel<<<n_items, 128, tc_gemm_smem_bytes(), s>>>(items, jobs, segs, err);
+}
+
+bool tc_gemm_prepare_grouped() {
+    static bool done = false;
+    if (done) return true;
+    if (cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc_gemm_smem_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaFuncSetAttribute(max dynamic smem) failed for tc_gemm_grouped_kernel");
+        return false;
+    }
+    done = true;
     return true;
 }
 

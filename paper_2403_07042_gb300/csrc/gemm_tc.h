@@ -38,6 +38,29 @@ bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_p
 // Launch on `s`; `err` receives kErrTimeout if a bounded wait ran out.
 void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s);
 
+// Grouped form: many independent products (instances of a batch) in one launch.  Each
+// work item is one 128 x 128 tile of one split-K slice of one job; all jobs of a launch
+// share the plane-segment list.
+struct GemmJob {
+    const CUtensorMap *map_a;  // device address of the job's A tensor map (64-byte aligned)
+    const CUtensorMap *map_b;
+    float *out;                // [splits][M][N]
+    int M, N, kb_per_seg, kb_per_split;
+};
+
+struct GemmItem {
+    int job, tile_m, tile_n, split;
+};
+
+struct TcSegs {
+    int nseg;
+    int a[kTcMaxSeg], b[kTcMaxSeg];
+};
+
+bool tc_gemm_prepare_grouped();
+void tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs,
+                            uint32_t *err, cudaStream_t s);
+
 size_t tc_gemm_smem_bytes();
 
 }  // namespace qed

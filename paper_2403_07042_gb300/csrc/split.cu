@@ -31,7 +31,49 @@
 
 namespace qed {
 
+// Device-side description of one instance (one model) for the grouped kernels.
+struct InstDesc {
+    int64_t D, Dp;
+    int splits1, splits2;   // split-K slices of GEMM1 / GEMM2
+    float inv_w;            // 1 / (s_Delta s_rho): GEMM1 sums -> W
+    float s_w;              // scale of the W planes
+    float inv_x;            // 1 / (s_W s_Delta): GEMM2 sums -> X
+    float s_rho;            // scale of the rho planes
+    float *part;            // split-K partial sums (GEMM1, then GEMM2)
+    float *w32, *wt32;
+    float4 *rho, *V;
+    const float4 *phase;
+    const float2 *damp;
+    const int32_t *in_ptr, *in_jump, *in_src;
+    const float2 *coef;
+    __half *rho_pl, *w_pl;
+};
+
+// 32 x 32 tiles of W (w_reduce) or 32 x 8 element blocks (form_v, dissipate) of one instance
+struct TileItem {
+    int inst, bx, by, pad;
+};
+
+// The grouped work of one or many instances: descriptors, GEMM jobs and work lists.
+struct Batch {
+    int n = 0;
+    InstDesc *desc = nullptr;
+    GemmJob *jobs1 = nullptr, *jobs2 = nullptr;
+    CUtensorMap *maps = nullptr;  // [4 n]: A1, B1, A2, B2 of each instance
+    GemmItem *items1 = nullptr, *items2 = nullptr;
+    int n_items1 = 0, n_items2 = 0;
+    TileItem *wtiles = nullptr, *etiles = nullptr;
+    int n_wtiles = 0, n_etiles = 0;
+    void release() {
+        void *ptrs[] = {desc, jobs1, jobs2, maps, items1, items2, wtiles, etiles};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        *this = Batch();
+    }
+};
+
 struct SplitState {
+    Batch self;               // this model as a batch of one
     int64_t Dp = 0;           // padded dimension (multiple of 128)
     int num_sms = 148;
     TcGemm g1, g2;
@@ -192,64 +234,60 @@ __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
 
 // W from the split-K partials of GEMM1 (rows r < Dp real, r >= Dp imaginary), in FP32:
 // writes W, its transpose (through a shared-memory tile so both stores coalesce) and its
-// FP16 hi/lo planes as GEMM2's A operand, row k = [W_re[k, :] | W_im[k, :]].
-__global__ void __launch_bounds__(256) w_reduce_kernel(int64_t Dp, int splits, const float *__restrict__ part,
-                                                       float inv_scale, float s_w, float *__restrict__ w32,
-                                                       float *__restrict__ wt32, __half *__restrict__ wpl) {
+// FP16 hi/lo planes as GEMM2's A operand, row k = [W_re[k, :] | W_im[k, :]].  One block
+// per 32 x 32 tile of one instance.
+__global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restrict__ tiles,
+                                                       const InstDesc *__restrict__ descs) {
     __shared__ float tre[32][33], tim[32][33];
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc &a = descs[it.inst];
+    const int64_t Dp = a.Dp;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int64_t k0 = (int64_t)blockIdx.y * 32, l0 = (int64_t)blockIdx.x * 32;
+    const int64_t k0 = (int64_t)it.by * 32, l0 = (int64_t)it.bx * 32;
     const int64_t stride = 2 * Dp * Dp, plane = Dp * 2 * Dp;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t k = k0 + ty + 8 * q, l = l0 + tx;
         float re = 0.f, im = 0.f;
-        for (int s = 0; s < splits; ++s) {
-            re += part[s * stride + k * Dp + l];
-            im += part[s * stride + (Dp + k) * Dp + l];
+        for (int s = 0; s < a.splits1; ++s) {
+            re += a.part[s * stride + k * Dp + l];
+            im += a.part[s * stride + (Dp + k) * Dp + l];
         }
-        re *= inv_scale;
-        im *= inv_scale;
-        w32[k * Dp + l] = re;
-        w32[Dp * Dp + k * Dp + l] = im;
+        re *= a.inv_w;
+        im *= a.inv_w;
+        a.w32[k * Dp + l] = re;
+        a.w32[Dp * Dp + k * Dp + l] = im;
         tre[ty + 8 * q][tx] = re;
         tim[ty + 8 * q][tx] = im;
-        const float xr = re * s_w, xi = im * s_w;
+        const float xr = re * a.s_w, xi = im * a.s_w;
         __half h = __float2half_rn(xr);
-        wpl[k * 2 * Dp + l] = h;
-        wpl[plane + k * 2 * Dp + l] = __float2half_rn(xr - __half2float(h));
+        a.w_pl[k * 2 * Dp + l] = h;
+        a.w_pl[plane + k * 2 * Dp + l] = __float2half_rn(xr - __half2float(h));
         h = __float2half_rn(xi);
-        wpl[k * 2 * Dp + Dp + l] = h;
-        wpl[plane + k * 2 * Dp + Dp + l] = __float2half_rn(xi - __half2float(h));
+        a.w_pl[k * 2 * Dp + Dp + l] = h;
+        a.w_pl[plane + k * 2 * Dp + Dp + l] = __float2half_rn(xi - __half2float(h));
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t l = l0 + ty + 8 * q, k = k0 + tx;
-        wt32[l * Dp + k] = tre[tx][ty + 8 * q];
-        wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + 8 * q];
+        a.wt32[l * Dp + k] = tre[tx][ty + 8 * q];
+        a.wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + 8 * q];
     }
 }
 
-struct FormArgs {
-    int64_t D, Dp;
-    int splits;
-    const float4 *rho;
-    float4 *V;
-    const float *w32, *wt32, *part;
-    float inv_x;  // 1 / (s_W s_Delta)
-    const float4 *phase;
-};
-
 // V_mn = P_m conj(P_n) (rho_mn + W_mn + conj(W_nm) + X_mn): the increment in FP32, the
-// sum and the phase in double-float.
-__global__ void __launch_bounds__(256) form_v_kernel(FormArgs a) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+// sum and the phase in double-float.  One block per 32 x 8 elements of one instance.
+__global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict__ tiles,
+                                                     const InstDesc *__restrict__ descs) {
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc &a = descs[it.inst];
+    const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
+    const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
     if (m >= a.D || n >= a.D) return;
     const int64_t Dp = a.Dp, stride = Dp * 2 * Dp;
     float xr = 0.f, xi = 0.f;
-    for (int s = 0; s < a.splits; ++s) {
+    for (int s = 0; s < a.splits2; ++s) {
         xr += a.part[s * stride + m * 2 * Dp + n];
         xi += a.part[s * stride + m * 2 * Dp + Dp + n];
     }
@@ -262,23 +300,15 @@ __global__ void __launch_bounds__(256) form_v_kernel(FormArgs a) {
     a.V[m * a.D + n] = store_cdf(cdf_mul(cdf_mul_conj(pm, pn), r));
 }
 
-struct DissArgs {
-    int64_t D, Dp;
-    const float4 *V;
-    float4 *rho;
-    const float2 *damp;
-    const int32_t *in_ptr, *in_jump, *in_src;
-    const float2 *coef;
-    float s_rho;
-    __half *pl;
-};
-
 // Eq. (3) on V: rho_mn = V_mn - (dt/2)(d_m + d_n) V_mn + dt sum_j c_j(m) c_j(n) V[src_j(m), src_j(n)];
 // the two correction terms (relative size dt gamma) are formed to FP32 accuracy and added
 // to the double-float V.  Also writes the FP16 planes of rho for the next GEMM1.
-__global__ void __launch_bounds__(256) dissipate_df_kernel(DissArgs a) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+__global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
+                                                           const InstDesc *__restrict__ descs) {
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc &a = descs[it.inst];
+    const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
+    const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
     if (m >= a.D || n >= a.D) return;
     const int64_t D = a.D;
     const cdf v = load_cdf(a.V[m * D + n]);
@@ -312,11 +342,11 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(DissArgs a) {
     const int64_t plane = a.Dp * 2 * a.Dp;
     __half h, l;
     df_to_half2(out.re, a.s_rho, h, l);
-    a.pl[m * 2 * a.Dp + n] = h;
-    a.pl[plane + m * 2 * a.Dp + n] = l;
+    a.rho_pl[m * 2 * a.Dp + n] = h;
+    a.rho_pl[plane + m * 2 * a.Dp + n] = l;
     df_to_half2(out.im, a.s_rho, h, l);
-    a.pl[m * 2 * a.Dp + a.Dp + n] = h;
-    a.pl[plane + m * 2 * a.Dp + a.Dp + n] = l;
+    a.rho_pl[m * 2 * a.Dp + a.Dp + n] = h;
+    a.rho_pl[plane + m * 2 * a.Dp + a.Dp + n] = l;
 }
 
 __global__ void __launch_bounds__(256) observables_df_kernel(int64_t D, const float4 *st, const double *w,
@@ -421,51 +451,123 @@ qed_status alloc(T **p, size_t count) {
         if (st_ != QED_OK) return st_;  \
     } while (0)
 
-void launch_w_reduce(qed_model *m, cudaStream_t s) {
-    SplitState &S = *m->sp;
-    dim3 grid((unsigned)(S.Dp / 32), (unsigned)(S.Dp / 32));
-    w_reduce_kernel<<<grid, dim3(32, 8), 0, s>>>(S.Dp, S.g1.splits, S.partial,
-                                                 (float)(1.0 / (S.scale_delta * S.scale_rho)), (float)S.scale_w,
-                                                 S.w32, S.wt32, S.w_pl);
-    count_launches(1);
+const TcSegs kSegs1 = {4, {0, 0, 1, 2, 0, 0}, {0, 1, 0, 0, 0, 0}};  // Delta(hi,mid,lo) x rho(hi,lo)
+const TcSegs kSegs2 = {3, {0, 1, 0, 0, 0, 0}, {0, 0, 1, 0, 0, 0}};  // W(hi,lo) x Delta(hi,mid,lo)
+
+template <class T>
+qed_status upload(T **dst, const std::vector<T> &v) {
+    SPLIT_TRY(alloc(dst, std::max<size_t>(v.size(), 1)));
+    if (!v.empty()) QED_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return QED_OK;
 }
 
-void launch_form(qed_model *m, cudaStream_t s) {
-    SplitState &S = *m->sp;
-    FormArgs a;
-    a.D = m->D;
-    a.Dp = S.Dp;
-    a.splits = S.g2.splits;
-    a.rho = S.rho_df[0];
-    a.V = S.rho_df[1];
-    a.w32 = S.w32;
-    a.wt32 = S.wt32;
-    a.part = S.partial;
-    a.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
-    a.phase = S.phase_df;
-    dim3 block(32, 8);
-    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
-    form_v_kernel<<<grid, block, 0, s>>>(a);
-    count_launches(1);
+// Descriptors, jobs and work lists of a batch.  With `single` set (one model on its own)
+// the GEMMs keep their split-K slices; in a batch every product runs unsplit, largest
+// first, since the batch itself fills the GPU.
+qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
+    b.release();
+    b.n = n;
+    std::vector<InstDesc> desc((size_t)n);
+    std::vector<GemmJob> jobs1((size_t)n), jobs2((size_t)n);
+    std::vector<CUtensorMap> maps((size_t)(4 * n));
+    std::vector<GemmItem> it1, it2;
+    std::vector<TileItem> wt, et;
+    for (int i = 0; i < n; ++i) {
+        qed_model *m = ms[i];
+        SplitState &S = *m->sp;
+        InstDesc &d = desc[(size_t)i];
+        d.D = m->D;
+        d.Dp = S.Dp;
+        d.splits1 = single ? S.g1.splits : 1;
+        d.splits2 = single ? S.g2.splits : 1;
+        d.inv_w = (float)(1.0 / (S.scale_delta * S.scale_rho));
+        d.s_w = (float)S.scale_w;
+        d.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
+        d.s_rho = (float)S.scale_rho;
+        d.part = S.partial;
+        d.w32 = S.w32;
+        d.wt32 = S.wt32;
+        d.rho = S.rho_df[0];
+        d.V = S.rho_df[1];
+        d.phase = S.phase_df;
+        d.damp = S.damp_df;
+        d.in_ptr = m->in_ptr;
+        d.in_jump = m->in_jump;
+        d.in_src = m->in_src;
+        d.coef = S.coef_df;
+        d.rho_pl = S.rho_pl;
+        d.w_pl = S.w_pl;
+        maps[(size_t)(4 * i + 0)] = S.g1.a;
+        maps[(size_t)(4 * i + 1)] = S.g1.b;
+        maps[(size_t)(4 * i + 2)] = S.g2.a;
+        maps[(size_t)(4 * i + 3)] = S.g2.b;
+        const TcGemm *gs[2] = {&S.g1, &S.g2};
+        GemmJob *js[2] = {&jobs1[(size_t)i], &jobs2[(size_t)i]};
+        std::vector<GemmItem> *its[2] = {&it1, &it2};
+        for (int q = 0; q < 2; ++q) {
+            const TcGemm &g = *gs[q];
+            const int splits = single ? g.splits : 1;
+            const int kb_total = g.nseg * (g.K / kTcBK);
+            js[q]->M = g.M;
+            js[q]->N = g.N;
+            js[q]->kb_per_seg = g.K / kTcBK;
+            js[q]->kb_per_split = single ? g.kb_per_split : kb_total;
+            js[q]->out = S.partial;
+            for (int sp = 0; sp < splits; ++sp)
+                for (int tm = 0; tm < g.M / kTcBM; ++tm)
+                    for (int tn = 0; tn < g.N / kTcBN; ++tn) its[q]->push_back({i, tm, tn, sp});
+        }
+        for (int by = 0; by < S.Dp / 32; ++by)
+            for (int bx = 0; bx < S.Dp / 32; ++bx) wt.push_back({i, bx, by, 0});
+        for (int by = 0; by < (m->D + 7) / 8; ++by)
+            for (int bx = 0; bx < (m->D + 31) / 32; ++bx) et.push_back({i, bx, by, 0});
+    }
+    if (!single) {
+        // longest products first, so the tail of the grouped launch is short
+        auto by_cost = [&](const GemmItem &x, const GemmItem &y) {
+            return jobs1[(size_t)x.job].kb_per_seg > jobs1[(size_t)y.job].kb_per_seg;
+        };
+        std::stable_sort(it1.begin(), it1.end(), by_cost);
+        std::stable_sort(it2.begin(), it2.end(), by_cost);
+    }
+    SPLIT_TRY(upload(&b.maps, maps));
+    for (int i = 0; i < n; ++i) {
+        jobs1[(size_t)i].map_a = b.maps + 4 * i + 0;
+        jobs1[(size_t)i].map_b = b.maps + 4 * i + 1;
+        jobs2[(size_t)i].map_a = b.maps + 4 * i + 2;
+        jobs2[(size_t)i].map_b = b.maps + 4 * i + 3;
+    }
+    SPLIT_TRY(upload(&b.desc, desc));
+    SPLIT_TRY(upload(&b.jobs1, jobs1));
+    SPLIT_TRY(upload(&b.jobs2, jobs2));
+    SPLIT_TRY(upload(&b.items1, it1));
+    SPLIT_TRY(upload(&b.items2, it2));
+    SPLIT_TRY(upload(&b.wtiles, wt));
+    SPLIT_TRY(upload(&b.etiles, et));
+    b.n_items1 = (int)it1.size();
+    b.n_items2 = (int)it2.size();
+    b.n_wtiles = (int)wt.size();
+    b.n_etiles = (int)et.size();
+    if (!tc_gemm_prepare_grouped()) return QED_ECUDA;
+    return QED_OK;
 }
 
-void launch_dissipate(qed_model *m, cudaStream_t s) {
-    SplitState &S = *m->sp;
-    DissArgs a;
-    a.D = m->D;
-    a.Dp = S.Dp;
-    a.V = S.rho_df[1];
-    a.rho = S.rho_df[0];
-    a.damp = S.damp_df;
-    a.in_ptr = m->in_ptr;
-    a.in_jump = m->in_jump;
-    a.in_src = m->in_src;
-    a.coef = S.coef_df;
-    a.s_rho = (float)S.scale_rho;
-    a.pl = S.rho_pl;
-    dim3 block(32, 8);
-    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
-    dissipate_df_kernel<<<grid, block, 0, s>>>(a);
+void launch_gemm1(const Batch &b, uint32_t *err, cudaStream_t s) {
+    tc_gemm_grouped_launch(b.items1, b.n_items1, b.jobs1, kSegs1, err, s);
+}
+void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
+    tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, err, s);
+}
+void launch_w_reduce(const Batch &b, cudaStream_t s) {
+    w_reduce_kernel<<<b.n_wtiles, dim3(32, 8), 0, s>>>(b.wtiles, b.desc);
+    count_launches(1);
+}
+void launch_form(const Batch &b, cudaStream_t s) {
+    form_v_kernel<<<b.n_etiles, dim3(32, 8), 0, s>>>(b.etiles, b.desc);
+    count_launches(1);
+}
+void launch_dissipate(const Batch &b, cudaStream_t s) {
+    dissipate_df_kernel<<<b.n_etiles, dim3(32, 8), 0, s>>>(b.etiles, b.desc);
     count_launches(1);
 }
 
@@ -498,6 +600,7 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
         // GEMM2: W (hi, lo) x Delta (hi, mid, lo): hi*hi + lo*hi + hi*mid
         const int seg2[6] = {0, 0, 1, 0, 0, 1};
+        static_assert(kTcMaxSeg >= 4, "segment lists");
         if (!tc_gemm_plan(S.g1, S.a1, 3, S.rho_pl, 2, (int)(2 * Dp), (int)Dp, (int)(2 * Dp), 4, seg1, S.num_sms))
             return QED_ECUDA;
         if (!tc_gemm_plan(S.g2, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), 3, seg2, S.num_sms))
@@ -553,7 +656,8 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
     static_planes_kernel<<<blocks_for((int64_t)W2, 256), 256, 0, s>>>(D, Dp, m->work1, S.scale_delta, S.a1, S.b2);
     count_launches(1);
     QED_CUDA_TRY(cudaGetLastError());
-    return QED_OK;
+    qed_model *self[1] = {m};
+    return build_batch(S.self, self, 1, true);
 }
 
 qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
@@ -565,27 +669,28 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
     return QED_OK;
 }
 
-void split_step(qed_model *m, cudaStream_t s) {
-    SplitState &S = *m->sp;
-    tc_gemm_launch(S.g1, S.partial, m->err, s);
-    launch_w_reduce(m, s);
-    tc_gemm_launch(S.g2, S.partial, m->err, s);
-    launch_form(m, s);
-    launch_dissipate(m, s);
+void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
+    launch_gemm1(b, err, s);
+    launch_w_reduce(b, s);
+    launch_gemm2(b, err, s);
+    launch_form(b, s);
+    launch_dissipate(b, s);
 }
 
+void split_step(qed_model *m, cudaStream_t s) { batch_step(m->sp->self, m->err, s); }
+
 int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
-    SplitState &S = *m->sp;
+    const Batch &b = m->sp->self;
     cudaEventRecord(m->ev[0], s);
-    tc_gemm_launch(S.g1, S.partial, m->err, s);
+    launch_gemm1(b, m->err, s);
     cudaEventRecord(m->ev[1], s);
-    launch_w_reduce(m, s);
+    launch_w_reduce(b, s);
     cudaEventRecord(m->ev[2], s);
-    tc_gemm_launch(S.g2, S.partial, m->err, s);
+    launch_gemm2(b, m->err, s);
     cudaEventRecord(m->ev[3], s);
-    launch_form(m, s);
+    launch_form(b, s);
     cudaEventRecord(m->ev[4], s);
-    launch_dissipate(m, s);
+    launch_dissipate(b, s);
     cudaEventRecord(m->ev[5], s);
     label = "gemm1_tc,w_reduce,gemm2_tc,form_v,dissipate";
     return 5;
@@ -612,9 +717,42 @@ void split_end(qed_model *m, double2 *rho, cudaStream_t s) {
     count_launches(1);
 }
 
+__global__ void populations_kernel(int64_t D, const float4 *st, double *out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D) return;
+    const float4 v = st[k * D + k];
+    out[k] = (double)v.x + (double)v.y;
+}
+
+void split_populations(qed_model *m, double *out, cudaStream_t s) {
+    populations_kernel<<<blocks_for(m->D, 256), 256, 0, s>>>(m->D, m->sp->rho_df[0], out);
+    count_launches(1);
+}
+
+qed_status split_batch_create(qed_model *const *ms, int n, Batch **out) {
+    Batch *b = new Batch();
+    qed_status st = build_batch(*b, ms, n, false);
+    if (st != QED_OK) {
+        b->release();
+        delete b;
+        return st;
+    }
+    *out = b;
+    return QED_OK;
+}
+
+void split_batch_step(const Batch *b, uint32_t *err, cudaStream_t s) { batch_step(*b, err, s); }
+
+void split_batch_destroy(Batch *b) {
+    if (!b) return;
+    b->release();
+    delete b;
+}
+
 void split_release(qed_model *m) {
     if (!m->sp) return;
     SplitState &S = *m->sp;
+    S.self.release();
     void *ptrs[] = {S.a1,        S.b2,        S.rho_pl,   S.w_pl,    S.w32,     S.wt32,
                     S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df};
     for (void *p : ptrs)

@@ -17,6 +17,13 @@ void split_renorm(qed_model *m, cudaStream_t s);
 void split_observables(qed_model *m, const int32_t *ids, int32_t n_obs, double *out, cudaStream_t s);
 void split_end(qed_model *m, double2 *rho, cudaStream_t s);              // internal state -> caller rho
 int split_step_timed(qed_model *m, cudaStream_t s, std::string &label);
+void split_populations(qed_model *m, double *out, cudaStream_t s);      // out[k] = rho_kk
+
+// Many split-precision models stepped together: one grouped launch per phase.
+struct Batch;
+qed_status split_batch_create(qed_model *const *ms, int n, Batch **out);
+void split_batch_step(const Batch *b, uint32_t *err, cudaStream_t s);
+void split_batch_destroy(Batch *b);
 void split_release(qed_model *m);
 
 }  // namespace qed
