@@ -44,6 +44,11 @@ def parse():
     p.add_argument("--fp64-qme-steps", type=int, default=200)
     p.add_argument("--cpu-sample", type=int, default=40, help="oracle QME steps in the CPU baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD,
+                   choices=[WORKLOAD, "jch2_d36", "lattice_32x32_d2049", "batched_chains",
+                            "adjoint_lattice_24x24_d1153"],
+                   help="the default is the headline workload; the others are measured with --workload")
+    p.add_argument("--instances", type=int, default=512, help="batched_chains: number of instances")
     return p.parse_args()
 
 
@@ -157,8 +162,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "QME steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "dim": D, "qme_steps_per_step": sample,
-                                        "precision": "fp64 (CPU oracle)"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "dim": D, "qme_steps_per_step": 10000,
+                                        "dt": 0.05, "record_every": 100, "precision": "fp64 (CPU oracle)",
+                                        "sample_qme_steps_per_step": sample},
         "complex_tflops": complex_tflops(D, value),
         "cpu_baseline": {"value": value, "unit": "QME steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample} QME steps of the dim-512 workload per bench step"},
@@ -328,8 +334,11 @@ def make_roofline(kern, D, precision):
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s"}
     if name.startswith("gemm"):
-        # executed MMA work: hi*hi + hi*lo + lo*hi over the real embedding (K' = 3 * 2D)
-        flops = 2.0 * (2 * D) * D * (6 * D)
+        # executed MMA work over the real embedding, padded Dp: GEMM1 (2Dp x Dp x 2Dp) with
+        # four FP16 plane products, GEMM2 (Dp x 2Dp x 2Dp) with three
+        Dp = -(-D // 128) * 128
+        segs = 4 if name.startswith("gemm1") else 3
+        flops = 2.0 * (2 * Dp) * Dp * (2 * Dp) * segs
         achieved = flops / (ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
         return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -356,9 +365,111 @@ def parity_against_golden(rho, records, qme_steps):
     return out
 
 
+def run_other(args):
+    """Secondary workloads (one GPU, no collectives): the dim-36 FP64 cavities, the 32 x 32
+    lattice, the batched chains and the adjoint lattice.  Same JSON fields; `config.workload`
+    names the workload."""
+    import torch
+
+    import paper_2403_07042_gb300 as qed
+    from paper_2403_07042_gb300 import build as qbuild
+
+    qbuild.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    wl = args.workload
+    prec = args.precision
+    extra = {}
+    if wl == "batched_chains":
+        specs = W.batched_chains(args.instances, seed=0)
+        steps = args.qme_steps or specs[0]["n_steps"]
+        models = [qed.Model(m, precision=prec) for m in specs]
+        dims = [gm.dim for gm in models]
+        rho0 = []
+        for gm in models:
+            r = torch.zeros((gm.dim, gm.dim), dtype=torch.complex128, device=dev)
+            i0 = gm.initial_index()
+            r[i0, i0] = 1.0
+            rho0.append(r)
+        rhos = [r.clone() for r in rho0]
+
+        def one():
+            for a, b in zip(rhos, rho0):
+                a.copy_(b)
+            qed.evolve_batched(models, rhos, steps)
+        flops = sum(16.0 * d ** 3 for d in dims)
+        unit = "instance QME steps/s"
+        per_step_units = len(models) * steps
+        extra["dims"] = {"min": min(dims), "max": max(dims), "mean": float(np.mean(dims)),
+                         "hist_128": np.histogram(dims, bins=range(0, 1153, 128))[0].tolist()}
+    else:
+        m = {"jch2_d36": W.jch_two_cavities, "lattice_32x32_d2049": W.lattice,
+             "adjoint_lattice_24x24_d1153": W.adjoint_lattice}[wl]()
+        steps = args.qme_steps or m["n_steps"]
+        gm = qed.Model(m, precision=prec)
+        D = gm.dim
+        rho0 = torch.zeros((D, D), dtype=torch.complex128, device=dev)
+        i0 = gm.initial_index()
+        rho0[i0, i0] = 1.0
+        rho = rho0.clone()
+        if wl == "adjoint_lattice_24x24_d1153":
+            # loss weights: the photon and the atom population of the corner cavity (0, 0)
+            photon, atom, _ = qed.digit_positions(m)
+            w = torch.zeros(D, dtype=torch.float64, device=dev)
+            for pos in (photon[0], atom[0]):
+                d = np.zeros(gm.n_digits, dtype=np.int32)
+                d[pos] = 1
+                w[gm.index_of(d)] = 1.0
+
+            def one():
+                gm.adjoint(rho0, steps, w, checkpoint_every=m["checkpoint_every"])
+            unit = "adjoint QME steps/s"
+        else:
+            r = m["record_every"]
+            rec = torch.zeros((gm.n_records(steps, r), D), dtype=torch.float64, device=dev)
+
+            def one():
+                rho.copy_(rho0)
+                gm.evolve(rho, steps, record_every=r, obs_ids=list(range(D)), records=rec)
+            unit = "QME steps/s"
+        flops = 16.0 * D ** 3
+        per_step_units = steps
+        extra["dim"] = D
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = qed.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        one()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = qed.launch_count() - launches0
+    clocks = sampler.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    value = args.steps * per_step_units / (t_ms / 1e3)
+    qme_rate = args.steps * steps / (t_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16x2->f32 (split), f64 master" if prec != "fp64" else "f64", "data": "synthetic",
+        "config": dict({"workload": wl, "qme_steps_per_step": steps, "precision": prec,
+                        "l2": "flushed (512 MB write) between timed iterations"}, **extra),
+        "complex_tflops": flops * qme_rate / 1e12, "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != WORKLOAD:
+        run_other(a)
     else:
         run_ours(a)
