@@ -1,18 +1,21 @@
 // tcgen05 / TMA / mbarrier GEMM for sm_103a (Blackwell): the dense products of the
 // "unitary evolution" stage (Sec. 4.2, Table 3) in split precision.
 //
-// One CTA computes one 128 x 128 FP32 tile of one split-K slice:
-//   warp 0, one lane : TMA producer, 6-stage ring of (A 128x64, B 128x64) FP16 tiles of the
-//                      current segment's planes,
+// One CTA computes one 128 x 256 FP32 tile of one split-K slice:
+//   warp 0, one lane : TMA producer, 4-stage ring of (A 128x64, B 256x64) FP16 tiles of the
+//                      current segment's planes (a last tile of 128 columns reads zeros),
 //                      128-byte swizzled, completion tracked by mbarrier transaction bytes
-//   warp 1, one lane : MMA issuer, tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
+//   warp 1, one lane : MMA issuer, tcgen05.mma.cta_group::1.kind::f16 (M=128, N=256, K=16)
 //                      into a TMEM accumulator; tcgen05.commit frees each smem stage
-//   warps 0-3        : epilogue, tcgen05.ld 32x32b (thread = accumulator row) -> global
+//   warps 0-3        : epilogue, tcgen05.ld 32x32b (thread = accumulator row), transposed
+//                      through shared memory so that each store writes 128 contiguous bytes
 // Every wait is bounded by a clock budget; on expiry the kernel records kErrTimeout,
 // stops issuing work, waits (bounded) for what it issued, frees TMEM and returns.
 #include <cstdio>
 #include <cstring>
 #include <string>
+
+#include <cuda_fp16.h>
 
 #include "gemm_tc.h"
 #include "kernels.h"
@@ -23,7 +26,6 @@ namespace qed {
 namespace {
 
 constexpr uint32_t kStageA = kTcBM * kTcBK * 2;  // bytes
-constexpr uint32_t kStageB = kTcBN * kTcBK * 2;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -125,16 +127,23 @@ struct Params {
     int kb_per_seg;
     int kb_total;
     int kb_per_split;
-    int seg_a[kTcMaxSeg], seg_b[kTcMaxSeg];
+    uint32_t seg_a, seg_b;  // plane of segment q in bits 3q..3q+2 (kept in registers)
+    int tx_bytes;
+    int mode;   // epilogue: kEpiPlain (slice split of out) or kEpiW (unsplit products only)
     float *out;
     uint32_t *err;
+    TcEpilogueW w;
 };
 
 // One 128 x 128 output tile of one split-K slice (the body shared by the single and the
 // grouped kernel).  tmA / tmB are generic addresses of tensor maps in parameter or global
 // memory.
+template <int BN>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const Params &p,
                                           int tile_m, int tile_n, int split) {
+    constexpr int kTcBN = BN;
+    constexpr int kTcStages = tc_stages(BN);
+    constexpr uint32_t kStageB = BN * kTcBK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
@@ -189,9 +198,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
             const int kb = kb0 + i;
             const int seg = kb / p.kb_per_seg, kk = kb % p.kb_per_seg;
             const uint32_t bar = full0 + 8 * s;
-            mbar_expect_tx(bar, kStageA + kStageB);
-            tma_load_3d(smem_u32(sA + s * kStageA), tmA, kk * kTcBK, tile_m * kTcBM, p.seg_a[seg], bar);
-            tma_load_3d(smem_u32(sB + s * kStageB), tmB, kk * kTcBK, tile_n * kTcBN, p.seg_b[seg], bar);
+            mbar_expect_tx(bar, (uint32_t)p.tx_bytes);
+            tma_load_3d(smem_u32(sA + s * kStageA), tmA, kk * kTcBK, tile_m * kTcBM, (p.seg_a >> (3 * seg)) & 7, bar);
+            tma_load_3d(smem_u32(sB + s * kStageB), tmB, kk * kTcBK, tile_n * kTcBN, (p.seg_b >> (3 * seg)) & 7, bar);
             *issued = i + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -225,16 +234,73 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     if (!ready && lane == 0) atomicOr(p.err, kErrTimeout);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncwarp();
-    if (ready && !*abort_flag && nkb > 0) {
-        const int row = tile_m * kTcBM + warp * 32 + lane;
-        float *dst = p.out + ((size_t)split * p.M + row) * p.N + (size_t)tile_n * kTcBN;
+    const bool ok = __all_sync(0xffffffffu, ready && !*abort_flag);
+    // register copies: the epilogue's global stores must not force reloads of p
+    const int mode = p.mode, pN = p.N;
+    float *const out = p.out + (int64_t)split * p.M * pN;  // this split-K slice
+    const int64_t Dp = p.w.Dp;
+    const float inv_w = p.w.inv_w, s_w = p.w.s_w;
+    float *const w32 = p.w.w32;
+    float *const wt32 = p.w.wt32;
+    __half *const w_pl = p.w.w_pl;
+    const int col0 = tile_n * BN;
+    const int ncols = min(BN, pN - col0);
+    const uint32_t tm_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const int64_t R0 = (int64_t)tile_m * kTcBM + warp * 32;  // output row of lane 0
+    // the stage buffers are free once every MMA of the CTA has completed
+    float *tbuf = (float *)sA + warp * (32 * 36);  // per-warp [32][36] transpose tile
+    if (ok) {
 #pragma unroll 1
-        for (int c = 0; c < kTcBN; c += 32) {
+        for (int c = 0; c < ncols; c += 32) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-            float4 *d4 = (float4 *)(dst + c);
+            tmem_ld32(tm_row + (uint32_t)c, v);
+            if (mode == kEpiW) {
+                // W^T straight from the rows: lanes hold consecutive k of one column
+                const int64_t R = R0 + lane;
+                const int64_t plane = R / Dp, k = R % Dp;
+                float *dst = wt32 + plane * Dp * Dp + (int64_t)(col0 + c) * Dp + k;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                for (int j = 0; j < 32; ++j) dst[(int64_t)j * Dp] = v[j] * inv_w;
+            }
+            // transpose through shared memory: row-major 16-byte pieces, 4 rows per store
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *(float4 *)(tbuf + lane * 36 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            __syncwarp();
+            const int sub = lane >> 3, col4 = 4 * (lane & 7);
+            if (mode == kEpiW) {
+                const int64_t plane = R0 / Dp;  // every row of a tile lies in one plane
+                const int64_t k0 = R0 % Dp, L = col0 + c + col4;
+                const int64_t lo_off = Dp * 2 * Dp;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int r = 4 * it + sub;
+                    float4 x = *(const float4 *)(tbuf + r * 36 + col4);
+                    x.x *= inv_w;
+                    x.y *= inv_w;
+                    x.z *= inv_w;
+                    x.w *= inv_w;
+                    *(float4 *)(w32 + plane * Dp * Dp + (k0 + r) * Dp + L) = x;
+                    const float a0 = x.x * s_w, a1 = x.y * s_w, a2 = x.z * s_w, a3 = x.w * s_w;
+                    const __half h0 = __float2half_rn(a0), h1 = __float2half_rn(a1), h2 = __float2half_rn(a2),
+                                 h3 = __float2half_rn(a3);
+                    __half2 hi[2] = {__halves2half2(h0, h1), __halves2half2(h2, h3)};
+                    __half2 lo[2] = {
+                        __halves2half2(__float2half_rn(a0 - __half2float(h0)), __float2half_rn(a1 - __half2float(h1))),
+                        __halves2half2(__float2half_rn(a2 - __half2float(h2)), __float2half_rn(a3 - __half2float(h3)))};
+                    __half *hp = w_pl + (k0 + r) * 2 * Dp + plane * Dp + L;
+                    *(uint2 *)hp = *(const uint2 *)hi;
+                    *(uint2 *)(hp + lo_off) = *(const uint2 *)lo;
+                }
+            } else {
+                float *op = out + (R0 * pN) + col0 + c + col4;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int r = 4 * it + sub;
+                    *(float4 *)(op + (int64_t)r * pN) = *(const float4 *)(tbuf + r * 36 + col4);
+                }
+            }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -250,13 +316,15 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     }
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB, Params p) {
-    gemm_tile(&tmA, &tmB, p, blockIdx.y, blockIdx.x, blockIdx.z);
+    gemm_tile<BN>(&tmA, &tmB, p, blockIdx.y, blockIdx.x, blockIdx.z);
 }
 
 // Grouped launch: CTA b computes work item items[b] of job items[b].job (one instance of
 // a batch), with that job's tensor maps read from global memory.
+template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_grouped_kernel(const GemmItem *__restrict__ items,
                                                                  const GemmJob *__restrict__ jobs, TcSegs segs,
                                                                  uint32_t *err) {
@@ -268,14 +336,19 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_grouped_kernel(const GemmItem 
     p.kb_per_seg = jb.kb_per_seg;
     p.kb_total = segs.nseg * jb.kb_per_seg;
     p.kb_per_split = jb.kb_per_split;
+    p.tx_bytes = jb.tx_bytes;
+    p.mode = jb.mode;
+    p.w = jb.w;
+    p.seg_a = 0;
+    p.seg_b = 0;
 #pragma unroll
     for (int q = 0; q < kTcMaxSeg; ++q) {
-        p.seg_a[q] = segs.a[q];
-        p.seg_b[q] = segs.b[q];
+        p.seg_a |= (uint32_t)segs.a[q] << (3 * q);
+        p.seg_b |= (uint32_t)segs.b[q] << (3 * q);
     }
     p.out = jb.out;
     p.err = err;
-    gemm_tile(jb.map_a, jb.map_b, p, it.tile_m, it.tile_n, it.split);
+    gemm_tile<BN>(jb.map_a, jb.map_b, p, it.tile_m, it.tile_n, it.split);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -320,14 +393,26 @@ bool encode(CUtensorMap *map, const void *base, int K, int rows, int planes, int
 
 }  // namespace
 
-size_t tc_gemm_smem_bytes() {
-    return 1024 + (size_t)kTcStages * (kStageA + kStageB) + (2 * kTcStages + 1) * 8 + 32;
+constexpr size_t stage_bytes(int bn) { return (size_t)tc_stages(bn) * (kStageA + (size_t)bn * kTcBK * 2); }
+static_assert((size_t)4 * 32 * 36 * 4 <= stage_bytes(128), "epilogue tiles must fit in the stage buffers");
+
+size_t tc_gemm_smem_bytes(int bn) { return 1024 + stage_bytes(bn) + (2 * tc_stages(bn) + 1) * 8 + 32; }
+
+template <class F>
+bool set_smem(F kernel, int bn) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_gemm_smem_bytes(bn)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaFuncSetAttribute(max dynamic smem) failed for the tcgen05 GEMM");
+        return false;
+    }
+    return true;
 }
 
 bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_planes, int planes_b, int M, int N,
-                  int K, int nseg, const int *seg_pairs, int num_sms, int force_splits) {
-    if (M % kTcBM || N % kTcBN || K % kTcBK || ((uintptr_t)a_planes & 15) || ((uintptr_t)b_planes & 15)) {
-        set_error("tc_gemm: shapes must be multiples of the tile and planes 16-byte aligned");
+                  int K, int nseg, const int *seg_pairs, int num_sms, int force_splits, int force_bn) {
+    if (M % kTcBM || N % 128 || K % kTcBK || ((uintptr_t)a_planes & 15) || ((uintptr_t)b_planes & 15)) {
+        set_error("tc_gemm: M and N must be multiples of 128, K of 64, planes 16-byte aligned");
         return false;
     }
     if (nseg < 1 || nseg > kTcMaxSeg || planes_a < 1 || planes_b < 1) {
@@ -347,46 +432,48 @@ bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_p
     g.M = M;
     g.N = N;
     g.K = K;
-    if (!encode(&g.a, a_planes, K, M, planes_a, kTcBM) || !encode(&g.b, b_planes, K, N, planes_b, kTcBN))
+    // wide tiles once they alone fill half the SMs, narrow ones below that
+    g.bn = force_bn ? force_bn : ((M / kTcBM) * ((N + 255) / 256) * 2 >= num_sms ? 256 : 128);
+    g.b_box_rows = N < g.bn ? N : g.bn;
+    if (!encode(&g.a, a_planes, K, M, planes_a, kTcBM) || !encode(&g.b, b_planes, K, N, planes_b, g.b_box_rows))
         return false;
-    const int tiles = (M / kTcBM) * (N / kTcBN);
+    const int tiles = (M / kTcBM) * ((N + g.bn - 1) / g.bn);
     const int kb_total = nseg * (K / kTcBK);
-    int splits = num_sms / tiles;
-    splits = splits < 1 ? 1 : splits;
-    const int max_splits = kb_total / 8 > 0 ? kb_total / 8 : 1;  // at least 8 k-blocks per slice
-    splits = splits > max_splits ? max_splits : splits;
+    // split-K slices (a power of two <= 4) while the tiles fill fewer
+    // than half the SMs and each slice keeps at least 4 k-blocks
+    int splits = 1;
+    while (splits < 4 && tiles * splits * 2 <= num_sms && kb_total / (splits * 2) >= 4) splits *= 2;
     if (force_splits > 0) splits = force_splits > kb_total ? kb_total : force_splits;
     g.kb_per_split = (kb_total + splits - 1) / splits;
     g.splits = (kb_total + g.kb_per_split - 1) / g.kb_per_split;
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_gemm_smem_bytes()) != cudaSuccess) {
-            set_error("cudaFuncSetAttribute(max dynamic smem) failed for tc_gemm_kernel");
-            cudaGetLastError();
-            return false;
-        }
+        if (!set_smem(tc_gemm_kernel<128>, 128) || !set_smem(tc_gemm_kernel<256>, 256)) return false;
         attr_set = true;
     }
     return true;
 }
 
-void tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs,
+template <int BN>
+void grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs, uint32_t *err,
+                    cudaStream_t s) {
+    tc_gemm_grouped_kernel<BN><<<n_items, 128, tc_gemm_smem_bytes(BN), s>>>(items, jobs, segs, err);
+}
+
+void tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs, int bn,
                             uint32_t *err, cudaStream_t s) {
     if (n_items <= 0) return;
     count_launches(1);
-    tc_gemm_grouped_kernel<<<n_items, 128, tc_gemm_smem_bytes(), s>>>(items, jobs, segs, err);
+    if (bn == 128)
+        grouped_launch<128>(items, n_items, jobs, segs, err, s);
+    else
+        grouped_launch<256>(items, n_items, jobs, segs, err, s);
 }
 
 bool tc_gemm_prepare_grouped() {
     static bool done = false;
     if (done) return true;
-    if (cudaFuncSetAttribute(tc_gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc_gemm_smem_bytes()) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("cudaFuncSetAttribute(max dynamic smem) failed for tc_gemm_grouped_kernel");
-        return false;
-    }
+    if (!set_smem(tc_gemm_grouped_kernel<128>, 128) || !set_smem(tc_gemm_grouped_kernel<256>, 256)) return false;
     done = true;
     return true;
 }
@@ -397,16 +484,24 @@ void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) 
     p.N = g.N;
     p.kb_per_seg = g.K / kTcBK;
     p.kb_total = g.nseg * p.kb_per_seg;
-    for (int q = 0; q < kTcMaxSeg; ++q) {
-        p.seg_a[q] = q < g.nseg ? g.seg_a[q] : 0;
-        p.seg_b[q] = q < g.nseg ? g.seg_b[q] : 0;
+    p.seg_a = 0;
+    p.seg_b = 0;
+    for (int q = 0; q < g.nseg; ++q) {
+        p.seg_a |= (uint32_t)g.seg_a[q] << (3 * q);
+        p.seg_b |= (uint32_t)g.seg_b[q] << (3 * q);
     }
     p.kb_per_split = g.kb_per_split;
+    p.tx_bytes = (int)kStageA + g.b_box_rows * kTcBK * 2;
+    p.mode = kEpiPlain;
+    p.w = TcEpilogueW();
     p.out = out;
     p.err = err;
-    dim3 grid(g.N / kTcBN, g.M / kTcBM, g.splits);
+    dim3 grid((g.N + g.bn - 1) / g.bn, g.M / kTcBM, g.splits);
     count_launches(1);
-    tc_gemm_kernel<<<grid, 128, tc_gemm_smem_bytes(), s>>>(g.a, g.b, p);
+    if (g.bn == 128)
+        tc_gemm_kernel<128><<<grid, 128, tc_gemm_smem_bytes(128), s>>>(g.a, g.b, p);
+    else
+        tc_gemm_kernel<256><<<grid, 128, tc_gemm_smem_bytes(256), s>>>(g.a, g.b, p);
 }
 
 }  // namespace qed

@@ -64,6 +64,9 @@ struct Batch {
     int n_items1 = 0, n_items2 = 0;
     TileItem *wtiles = nullptr, *etiles = nullptr;
     int n_wtiles = 0, n_etiles = 0;
+    int cs1 = 1, cs2 = 1;  // split-K slices of GEMM1 / GEMM2
+    bool w_reduce = false;  // GEMM1 split: a separate pass sums its slices into W
+    int bn1 = 256, bn2 = 256;  // tile widths (one per grouped launch)
     void release() {
         void *ptrs[] = {desc, jobs1, jobs2, maps, items1, items2, wtiles, etiles};
         for (void *p : ptrs)
@@ -85,7 +88,7 @@ struct SplitState {
     __half *w_pl = nullptr;   // rows k: [W_re | W_im]
     float *w32 = nullptr;     // [2][Dp][Dp]  W (re plane, im plane)
     float *wt32 = nullptr;    // [2][Dp][Dp]  W^T (re plane, im plane)
-    float *partial = nullptr; // split-K partial sums of either product
+    float *partial = nullptr; // split-K slices of either product; GEMM2's sum X at slice 0
     float4 *rho_df[2] = {nullptr, nullptr};  // D x D {re_hi, re_lo, im_hi, im_lo}: rho, then V
     float4 *phase_df = nullptr;              // D: P_k as {re_hi, re_lo, im_hi, im_lo}
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
@@ -478,8 +481,8 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         InstDesc &d = desc[(size_t)i];
         d.D = m->D;
         d.Dp = S.Dp;
-        d.splits1 = single ? S.g1.splits : 1;
-        d.splits2 = single ? S.g2.splits : 1;
+        d.splits1 = single ? S.g1.splits : 1;  // split-K slices summed by w_reduce
+        d.splits2 = single ? S.g2.splits : 1;  // and by form_v
         d.inv_w = (float)(1.0 / (S.scale_delta * S.scale_rho));
         d.s_w = (float)S.scale_w;
         d.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
@@ -497,11 +500,21 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.coef = S.coef_df;
         d.rho_pl = S.rho_pl;
         d.w_pl = S.w_pl;
-        maps[(size_t)(4 * i + 0)] = S.g1.a;
-        maps[(size_t)(4 * i + 1)] = S.g1.b;
-        maps[(size_t)(4 * i + 2)] = S.g2.a;
-        maps[(size_t)(4 * i + 3)] = S.g2.b;
-        const TcGemm *gs[2] = {&S.g1, &S.g2};
+        // a model on its own keeps its plans; in a batch every product runs unsplit with the
+        // wide tile, so one grouped launch serves all instances
+        TcGemm bg1 = S.g1, bg2 = S.g2;
+        if (!single) {
+            const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
+            const int seg2[6] = {0, 0, 1, 0, 0, 1};
+            if (!tc_gemm_plan(bg1, S.a1, 3, S.rho_pl, 2, S.g1.M, S.g1.N, S.g1.K, 4, seg1, 1, 1, kTcBNMax) ||
+                !tc_gemm_plan(bg2, S.w_pl, 2, S.b2, 3, S.g2.M, S.g2.N, S.g2.K, 3, seg2, 1, 1, kTcBNMax))
+                return QED_ECUDA;
+        }
+        maps[(size_t)(4 * i + 0)] = bg1.a;
+        maps[(size_t)(4 * i + 1)] = bg1.b;
+        maps[(size_t)(4 * i + 2)] = bg2.a;
+        maps[(size_t)(4 * i + 3)] = bg2.b;
+        const TcGemm *gs[2] = {&bg1, &bg2};
         GemmJob *js[2] = {&jobs1[(size_t)i], &jobs2[(size_t)i]};
         std::vector<GemmItem> *its[2] = {&it1, &it2};
         for (int q = 0; q < 2; ++q) {
@@ -513,9 +526,28 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
             js[q]->kb_per_seg = g.K / kTcBK;
             js[q]->kb_per_split = single ? g.kb_per_split : kb_total;
             js[q]->out = S.partial;
-            for (int sp = 0; sp < splits; ++sp)
-                for (int tm = 0; tm < g.M / kTcBM; ++tm)
-                    for (int tn = 0; tn < g.N / kTcBN; ++tn) its[q]->push_back({i, tm, tn, sp});
+            js[q]->tx_bytes = kTcBM * kTcBK * 2 + g.b_box_rows * kTcBK * 2;
+            // an unsplit GEMM1 writes W, W^T and the W planes itself; split products
+            // leave their slices to w_reduce / form_v
+            js[q]->mode = q == 0 && splits == 1 ? kEpiW : kEpiPlain;
+            js[q]->w = TcEpilogueW();
+            if (js[q]->mode == kEpiW) {
+                js[q]->w.Dp = S.Dp;
+                js[q]->w.inv_w = d.inv_w;
+                js[q]->w.s_w = d.s_w;
+                js[q]->w.w32 = S.w32;
+                js[q]->w.wt32 = S.wt32;
+                js[q]->w.w_pl = S.w_pl;
+            }
+            // the slices of one tile are consecutive: they form one cluster
+            for (int tm = 0; tm < g.M / kTcBM; ++tm)
+                for (int tn = 0; tn < (g.N + g.bn - 1) / g.bn; ++tn)
+                    for (int sp = 0; sp < splits; ++sp) its[q]->push_back({i, tm, tn, sp});
+            if (i == 0) {
+                (q == 0 ? b.cs1 : b.cs2) = splits;
+                (q == 0 ? b.bn1 : b.bn2) = g.bn;
+            }
+            if (q == 0 && splits > 1) b.w_reduce = true;
         }
         for (int by = 0; by < S.Dp / 32; ++by)
             for (int bx = 0; bx < S.Dp / 32; ++bx) wt.push_back({i, bx, by, 0});
@@ -553,10 +585,10 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
 }
 
 void launch_gemm1(const Batch &b, uint32_t *err, cudaStream_t s) {
-    tc_gemm_grouped_launch(b.items1, b.n_items1, b.jobs1, kSegs1, err, s);
+    tc_gemm_grouped_launch(b.items1, b.n_items1, b.jobs1, kSegs1, b.bn1, err, s);
 }
 void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
-    tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, err, s);
+    tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, err, s);
 }
 void launch_w_reduce(const Batch &b, cudaStream_t s) {
     w_reduce_kernel<<<b.n_wtiles, dim3(32, 8), 0, s>>>(b.wtiles, b.desc);
@@ -607,6 +639,7 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
             return QED_ECUDA;
         const size_t partial = (size_t)std::max(S.g1.splits, S.g2.splits) * 2 * Dp * Dp;
         SPLIT_TRY(alloc(&S.partial, partial));
+
         // per-row phases P_k as double-floats
         std::vector<double2> ph((size_t)D);
         QED_CUDA_TRY(cudaMemcpy(ph.data(), m->phase, (size_t)D * sizeof(double2), cudaMemcpyDeviceToHost));
@@ -670,8 +703,8 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
 }
 
 void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
-    launch_gemm1(b, err, s);
-    launch_w_reduce(b, s);
+    launch_gemm1(b, err, s);  // unsplit: its epilogue writes W, W^T and the W planes
+    if (b.w_reduce) launch_w_reduce(b, s);
     launch_gemm2(b, err, s);
     launch_form(b, s);
     launch_dissipate(b, s);
@@ -684,7 +717,7 @@ int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
     cudaEventRecord(m->ev[0], s);
     launch_gemm1(b, m->err, s);
     cudaEventRecord(m->ev[1], s);
-    launch_w_reduce(b, s);
+    if (b.w_reduce) launch_w_reduce(b, s);
     cudaEventRecord(m->ev[2], s);
     launch_gemm2(b, m->err, s);
     cudaEventRecord(m->ev[3], s);
