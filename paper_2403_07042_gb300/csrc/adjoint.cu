@@ -20,8 +20,12 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
+#include "gemm_tc.h"
 #include "kernels.h"
 #include "model.h"
+#include "split.h"
 
 namespace qed {
 
@@ -39,6 +43,16 @@ struct AdjointState {
     int32_t n_g = 0, n_zeta = 0;
     double2 *H = nullptr;  // dense H (device)
     double h_norm1 = 0.0;
+    int32_t n_out = 0;
+    // split precision: the backward model (U^+, conjugate phases, outgoing jump lists),
+    // whose step kappa -> J^+(U^+ kappa U) is the co-state step, and the tensor-core
+    // product rho_n lambda_n
+    qed_model *twin = nullptr;
+    __half *a_pl = nullptr;   // [2][Dp][2Dp]   rows m: [rho_re | rho_im]
+    __half *b_pl = nullptr;   // [2][2Dp][2Dp]  [[lam_re, lam_im], [-lam_im, lam_re]]
+    float *c_slices = nullptr;
+    TcGemm g;
+    int64_t Dp = 0;
 };
 
 namespace {
@@ -87,6 +101,7 @@ qed_status setup(qed_model *m) {
         }
         ptr[(size_t)k + 1] = (int32_t)jj.size();
     }
+    a->n_out = (int32_t)jj.size();
     ADJ_TRY(up(&a->out_ptr, ptr));
     ADJ_TRY(up(&a->out_jump, jj));
     ADJ_TRY(up(&a->out_dst, dst));
@@ -254,15 +269,355 @@ struct Buffers {
     }
 };
 
+// ---------------------------------------------------------------- split precision
+__global__ void conj_transpose_kernel(int64_t D, const double2 *U, double2 *Ut) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * D) return;
+    const int64_t r = idx / D, c = idx % D;
+    const double2 u = U[c * D + r];
+    Ut[idx] = make_double2(u.x, -u.y);
+}
+
+__global__ void conj_kernel(int64_t n, const double2 *x, double2 *y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = make_double2(x[i].x, -x[i].y);
+}
+
+__global__ void set_diag_df_kernel(int64_t D, const double *o, float4 *X) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * D) return;
+    const int64_t r = idx / D, c = idx % D;
+    float h = 0.f, l = 0.f;
+    if (r == c) {
+        h = (float)o[r];
+        l = (float)(o[r] - (double)h);
+    }
+    X[idx] = make_float4(h, l, 0.f, 0.f);
+}
+
+__device__ __forceinline__ double2 dfc(const float4 v) {
+    return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+__global__ void __launch_bounds__(256) loss_df_kernel(int64_t D, const float4 *st, const double *o, double *loss) {
+    __shared__ double part[256];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int64_t k = t; k < D; k += blockDim.x) s += o[k] * dfc(st[k * D + k]).x;
+    part[t] = s;
+    __syncthreads();
+    for (int st2 = blockDim.x / 2; st2 > 0; st2 >>= 1) {
+        if (t < st2) part[t] += part[t + st2];
+        __syncthreads();
+    }
+    if (t == 0) *loss = part[0];
+}
+
+__global__ void rowdot_df_kernel(int64_t D, const float4 *lam, const float4 *V, double *r) {
+    const int64_t k = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (k >= D) return;
+    double s = 0.0;
+    for (int64_t n = lane; n < D; n += 32) {
+        const double2 a = dfc(lam[k * D + n]), b = dfc(V[k * D + n]);
+        s += a.x * b.x + a.y * b.y;
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) r[k] = s;
+}
+
+__global__ void __launch_bounds__(256) gamma_grad_df_kernel(int64_t D, const int32_t *je_ptr, const int32_t *je_src,
+                                                            const int32_t *je_dst, const double *je_coef,
+                                                            const float4 *lam, const float4 *V, const double *r,
+                                                            double dt, double *grad) {
+    __shared__ double part[256];
+    const int j = blockIdx.x;
+    const int t = threadIdx.x;
+    const int64_t e0 = je_ptr[j], ne = je_ptr[j + 1] - e0;
+    double s = 0.0;
+    for (int64_t idx = t; idx < ne * ne; idx += blockDim.x) {
+        const int64_t e = e0 + idx / ne, f = e0 + idx % ne;
+        const double2 l = dfc(lam[(int64_t)je_dst[f] * D + je_dst[e]]);
+        const double2 v = dfc(V[(int64_t)je_src[e] * D + je_src[f]]);
+        s += je_coef[e] * je_coef[f] * (l.x * v.x - l.y * v.y);
+    }
+    for (int64_t e = e0 + t; e < e0 + ne; e += blockDim.x) s -= je_coef[e] * je_coef[e] * r[je_src[e]];
+    part[t] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (t < st) part[t] += part[t + st];
+        __syncthreads();
+    }
+    if (t == 0) grad[j] += dt * part[0];
+}
+
+__device__ __forceinline__ void half2_of(float4 v, bool im, float s, __half &h, __half &l) {
+    const float hi = (im ? v.z : v.x) * s, lo = (im ? v.w : v.y) * s;
+    h = __float2half_rn(hi);
+    l = __float2half_rn((hi - __half2float(h)) + lo);
+}
+
+// A planes of rho_n: rows m = [rho_re[m, :] | rho_im[m, :]] (Dp x 2Dp), hi / lo
+__global__ void a_planes_kernel(int64_t D, int64_t Dp, const float4 *st, float s, __half *pl) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = blockIdx.y;
+    if (n >= D) return;
+    const float4 v = st[m * D + n];
+    const int64_t plane = Dp * 2 * Dp;
+    __half h, l;
+    half2_of(v, false, s, h, l);
+    pl[m * 2 * Dp + n] = h;
+    pl[plane + m * 2 * Dp + n] = l;
+    half2_of(v, true, s, h, l);
+    pl[m * 2 * Dp + Dp + n] = h;
+    pl[plane + m * 2 * Dp + Dp + n] = l;
+}
+
+// B planes of lambda_n: [[lam_re, lam_im], [-lam_im, lam_re]] (2Dp x 2Dp), hi / lo.  The
+// product takes B transposed (K-major); for Hermitian lambda that is the same matrix.
+__global__ void b_planes_kernel(int64_t D, int64_t Dp, const float4 *lam, float s, __half *pl) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = blockIdx.y;
+    if (n >= D) return;
+    const float4 v = lam[m * D + n];
+    const float4 neg = make_float4(-v.x, -v.y, -v.z, -v.w);
+    const int64_t W2 = 2 * Dp, plane = W2 * W2;
+    __half h, l;
+    half2_of(v, false, s, h, l);  // re, upper left and lower right
+    pl[m * W2 + n] = h;
+    pl[plane + m * W2 + n] = l;
+    pl[(Dp + m) * W2 + Dp + n] = h;
+    pl[plane + (Dp + m) * W2 + Dp + n] = l;
+    half2_of(v, true, s, h, l);  // im, upper right
+    pl[m * W2 + Dp + n] = h;
+    pl[plane + m * W2 + Dp + n] = l;
+    half2_of(neg, true, s, h, l);  // -im, lower left
+    pl[(Dp + m) * W2 + n] = h;
+    pl[plane + (Dp + m) * W2 + n] = l;
+}
+
+// Nacc += (sum of the slices) / scale, the product being [C_re | C_im] (Dp x 2Dp)
+__global__ void acc_kernel(int64_t D, int64_t Dp, int splits, const float *sl, double inv, double2 *Nacc) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = blockIdx.y;
+    if (n >= D) return;
+    double re = 0.0, im = 0.0;
+    const int64_t stride = Dp * 2 * Dp;
+    for (int q = 0; q < splits; ++q) {
+        re += sl[q * stride + m * 2 * Dp + n];
+        im += sl[q * stride + m * 2 * Dp + Dp + n];
+    }
+    double2 a = Nacc[m * D + n];
+    a.x += re * inv;
+    a.y += im * inv;
+    Nacc[m * D + n] = a;
+}
+
+qed_status make_twin(qed_model *m, cudaStream_t s) {
+    AdjointState &a = *m->adj;
+    if (a.twin) return QED_OK;
+    qed_model *t = new qed_model();
+    a.twin = t;
+    const int64_t D = m->D;
+    const size_t DD = (size_t)(D * D);
+    t->D = D;
+    t->dt = m->dt;
+    t->prec = m->prec;
+    t->renorm_every = 0;
+    auto get = [&](void **p, size_t bytes) -> qed_status {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc failed for the backward model");
+            return QED_ENOMEM;
+        }
+        return QED_OK;
+    };
+    ADJ_TRY(get((void **)&t->U, DD * 16));
+    ADJ_TRY(get((void **)&t->work1, DD * 16));
+    ADJ_TRY(get((void **)&t->work2, DD * 16));
+    ADJ_TRY(get((void **)&t->phase, (size_t)D * 16));
+    ADJ_TRY(get((void **)&t->anti, (size_t)D * 8));
+    ADJ_TRY(get((void **)&t->in_ptr, (size_t)(D + 1) * 4));
+    ADJ_TRY(get((void **)&t->in_jump, (size_t)a.n_out * 4));
+    ADJ_TRY(get((void **)&t->in_src, (size_t)a.n_out * 4));
+    ADJ_TRY(get((void **)&t->in_coef, (size_t)a.n_out * 8));
+    ADJ_TRY(get((void **)&t->scalars, 16 * 8));
+    ADJ_TRY(get((void **)&t->err, 4));
+    QED_CUDA_TRY(cudaMallocHost((void **)&t->err_host, sizeof(uint32_t)));
+    QED_CUDA_TRY(cudaMemsetAsync(t->err, 0, 4, s));
+    t->n_in = a.n_out;
+    conj_transpose_kernel<<<blocks_for((int64_t)DD, 256), 256, 0, s>>>(D, m->U, t->U);
+    conj_kernel<<<blocks_for(D, 256), 256, 0, s>>>(D, m->phase, t->phase);
+    count_launches(2);
+    QED_CUDA_TRY(cudaMemcpyAsync(t->anti, m->anti, (size_t)D * 8, cudaMemcpyDeviceToDevice, s));
+    QED_CUDA_TRY(cudaMemcpyAsync(t->in_ptr, a.out_ptr, (size_t)(D + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (a.n_out > 0) {
+        QED_CUDA_TRY(cudaMemcpyAsync(t->in_jump, a.out_jump, (size_t)a.n_out * 4, cudaMemcpyDeviceToDevice, s));
+        QED_CUDA_TRY(cudaMemcpyAsync(t->in_src, a.out_dst, (size_t)a.n_out * 4, cudaMemcpyDeviceToDevice, s));
+        QED_CUDA_TRY(cudaMemcpyAsync(t->in_coef, a.out_coef, (size_t)a.n_out * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    ADJ_TRY(split_prepare(t, s));
+    // the product rho_n lambda_n
+    a.Dp = (D + kTcBM - 1) / kTcBM * kTcBM;
+    const int64_t Dp = a.Dp;
+    ADJ_TRY(get((void **)&a.a_pl, (size_t)2 * Dp * 2 * Dp * 2));
+    ADJ_TRY(get((void **)&a.b_pl, (size_t)2 * (2 * Dp) * (2 * Dp) * 2));
+    QED_CUDA_TRY(cudaMemset(a.a_pl, 0, (size_t)2 * Dp * 2 * Dp * 2));
+    QED_CUDA_TRY(cudaMemset(a.b_pl, 0, (size_t)2 * (2 * Dp) * (2 * Dp) * 2));
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int seg[6] = {0, 0, 0, 1, 1, 0};
+    if (!tc_gemm_plan(a.g, a.a_pl, 2, a.b_pl, 2, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), 3, seg, sms))
+        return QED_ECUDA;
+    ADJ_TRY(get((void **)&a.c_slices, (size_t)a.g.splits * Dp * 2 * Dp * 4));
+    return QED_OK;
+}
+
+// G = L_exp(X, M) as the upper-right block of exp([[X, tau M], [0, X]]) (tau a power of two
+// balancing the blocks' norms), contracted with dH/dtheta for every g and zeta.
+qed_status frechet_gradients(qed_model *m, Buffers &B, const double2 *Macc, double *grad_g, double *grad_zeta,
+                             cudaStream_t s) {
+    AdjointState &a = *m->adj;
+    const int64_t D = m->D;
+    const size_t DD = (size_t)(D * D);
+    const double dt = m->dt;
+    if (a.n_g + a.n_zeta > 0) {
+        std::vector<double2> hM(DD);
+        QED_CUDA_TRY(cudaMemcpyAsync(hM.data(), Macc, DD * 16, cudaMemcpyDeviceToHost, s));
+        QED_CUDA_TRY(cudaStreamSynchronize(s));
+        double mnorm = 0.0;
+        for (int64_t cc = 0; cc < D; ++cc) {
+            double col = 0.0;
+            for (int64_t rr = 0; rr < D; ++rr) col += std::hypot(hM[(size_t)(rr * D + cc)].x, hM[(size_t)(rr * D + cc)].y);
+            mnorm = std::max(mnorm, col);
+        }
+        const double xnorm = dt * a.h_norm1;
+        double tau = 1.0;
+        if (mnorm > 0.0 && xnorm > 0.0) tau = std::ldexp(1.0, (int)std::floor(std::log2(xnorm / mnorm)));
+        double2 *blk = nullptr, *R = nullptr;
+        ADJ_TRY(B.get(&blk, 4 * DD));
+        ADJ_TRY(B.get(&R, 4 * DD));
+        block_kernel<<<blocks_for((int64_t)(4 * DD), 256), 256, 0, s>>>(D, a.H, dt, Macc, tau, blk);
+        count_launches(1);
+        ADJ_TRY(expm_pade13(s, 2 * D, blk, xnorm + tau * mnorm, R, m->err));
+        const int np = a.n_g + a.n_zeta;
+        param_grad_kernel<<<blocks_for(np, 128), 128, 0, s>>>(D, np, a.pe_ptr, a.pe_row, a.pe_col, a.pe_unit, R,
+                                                              2.0 * dt / tau, grad_g, a.n_g, grad_zeta);
+        count_launches(1);
+    }
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    QED_CUDA_TRY(cudaGetLastError());
+    return QED_OK;
+}
+
+// The adjoint on the split-precision path: the forward steps and the segment recomputes
+// are qed_evolve's steps, the co-state steps are the backward model's steps, and
+// M = (sum_n rho_n lambda_n) U^+ is accumulated from one tensor-core product per step.
+qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, const double *obs_diag, double *loss,
+                         double *grad_g, double *grad_zeta, double *grad_gamma, cudaStream_t s) {
+    ADJ_TRY(make_twin(m, s));
+    AdjointState &a = *m->adj;
+    qed_model *t = a.twin;
+    k = std::min<int64_t>(k, std::max<int64_t>(N, 1));
+    const int64_t D = m->D, Dp = a.Dp;
+    const size_t DD = (size_t)(D * D);
+    const int64_t n_ck = N > 0 ? (N - 1) / k + 1 : 0;
+    const double dt = m->dt;
+    // The co-state is linear in o: run it for o / 2^e with max |o / 2^e| in (1/2, 1], so that
+    // |lambda_kl| <= 1 like |rho_kl| (the co-state map is unital and contractive) and the
+    // backward model's FP16 scales hold, and scale the gradients by 2^e.
+    std::vector<double> ho((size_t)D);
+    QED_CUDA_TRY(cudaMemcpyAsync(ho.data(), obs_diag, (size_t)D * 8, cudaMemcpyDeviceToHost, s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    double omax = 0.0;
+    for (double x : ho) omax = std::max(omax, std::abs(x));
+    const int e = omax > 0.0 ? (int)std::ceil(std::log2(omax)) : 0;
+    const double o_scale = std::ldexp(1.0, e);
+    for (double &x : ho) x = std::ldexp(x, -e);
+    const double s_a = std::ldexp(1.0, 14), s_b = std::ldexp(1.0, 14);
+    Buffers B;
+    float4 *ck = nullptr, *seg_rho = nullptr, *seg_v = nullptr;
+    double2 *Nacc = nullptr, *Macc = nullptr;
+    double *r = nullptr, *o_s = nullptr;
+    ADJ_TRY(B.get(&o_s, (size_t)D));
+    QED_CUDA_TRY(cudaMemcpyAsync(o_s, ho.data(), (size_t)D * 8, cudaMemcpyHostToDevice, s));
+    ADJ_TRY(B.get(&ck, DD * (size_t)std::max<int64_t>(n_ck, 1)));
+    ADJ_TRY(B.get(&seg_rho, DD * (size_t)k));
+    ADJ_TRY(B.get(&seg_v, DD * (size_t)k));
+    ADJ_TRY(B.get(&Nacc, DD));
+    ADJ_TRY(B.get(&Macc, DD));
+    ADJ_TRY(B.get(&r, (size_t)D));
+    // forward with checkpoints of the double-float state
+    ADJ_TRY(split_begin(m, (const double2 *)rho0, s));
+    for (int64_t n = 0; n < N; ++n) {
+        if (n % k == 0)
+            QED_CUDA_TRY(cudaMemcpyAsync(ck + (size_t)(n / k) * DD, split_state(m), DD * 16, cudaMemcpyDeviceToDevice, s));
+        split_step(m, s);
+    }
+    loss_df_kernel<<<1, 256, 0, s>>>(D, split_state(m), obs_diag, loss);
+    // co-state: lambda_N = diag(o) in the backward model's V buffer, kappa_N = J^+(lambda_N)
+    set_diag_df_kernel<<<blocks_for((int64_t)DD, 256), 256, 0, s>>>(D, o_s, split_vbuf(t));
+    count_launches(2);
+    split_dissipate_only(t, s);
+    QED_CUDA_TRY(cudaMemsetAsync(Nacc, 0, DD * 16, s));
+    if (a.n_jumps > 0) QED_CUDA_TRY(cudaMemsetAsync(grad_gamma, 0, (size_t)a.n_jumps * 8, s));
+    const dim3 rows(blocks_for(D, 256), (unsigned)D);
+    for (int64_t c = n_ck - 1; c >= 0; --c) {
+        const int64_t s0 = c * k, s1 = std::min(N, s0 + k);
+        QED_CUDA_TRY(cudaMemcpyAsync(split_state(m), ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
+        split_refresh_planes(m, s);
+        for (int64_t n = s0; n < s1; ++n) {
+            QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + (size_t)(n - s0) * DD, split_state(m), DD * 16,
+                                         cudaMemcpyDeviceToDevice, s));
+            split_step(m, s);
+            QED_CUDA_TRY(cudaMemcpyAsync(seg_v + (size_t)(n - s0) * DD, split_vbuf(m), DD * 16,
+                                         cudaMemcpyDeviceToDevice, s));
+        }
+        for (int64_t n = s1 - 1; n >= s0; --n) {
+            const float4 *rn = seg_rho + (size_t)(n - s0) * DD, *vn = seg_v + (size_t)(n - s0) * DD;
+            if (a.n_jumps > 0) {  // lambda_{n+1} is still in the backward model's V buffer
+                rowdot_df_kernel<<<blocks_for(D, 8), 256, 0, s>>>(D, split_vbuf(t), vn, r);
+                gamma_grad_df_kernel<<<a.n_jumps, 256, 0, s>>>(D, a.je_ptr, a.je_src, a.je_dst, a.je_coef,
+                                                               split_vbuf(t), vn, r, dt * o_scale, grad_gamma);
+                count_launches(2);
+            }
+            split_step(t, s);  // kappa_{n+1} -> lambda_n (V buffer) -> kappa_n (state)
+            // Nacc += rho_n lambda_n on the tensor cores
+            a_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, rn, (float)s_a, a.a_pl);
+            b_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, split_vbuf(t), (float)s_b, a.b_pl);
+            count_launches(2);
+            tc_gemm_launch(a.g, a.c_slices, m->err, s);
+            acc_kernel<<<rows, 256, 0, s>>>(D, Dp, a.g.splits, a.c_slices, o_scale / (s_a * s_b), Nacc);
+            count_launches(1);
+        }
+    }
+    // M = Nacc U^+, then the Frechet contraction
+    zgemm(s, D, D, D, 1.0, Nacc, D, m->U, D, true, 0.0, Macc, D);
+    ADJ_TRY(frechet_gradients(m, B, Macc, grad_g, grad_zeta, s));
+    uint32_t flags[2] = {0, 0};
+    QED_CUDA_TRY(cudaMemcpy(&flags[0], m->err, 4, cudaMemcpyDeviceToHost));
+    QED_CUDA_TRY(cudaMemcpy(&flags[1], t->err, 4, cudaMemcpyDeviceToHost));
+    if ((flags[0] | flags[1]) & kErrTimeout) {
+        QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+        QED_CUDA_TRY(cudaMemset(t->err, 0, 4));
+        set_error("qed_adjoint: a bounded device wait ran out");
+        return QED_ETIMEOUT;
+    }
+    return QED_OK;
+}
+
 }  // namespace
 
 void adjoint_release(qed_model *m) {
     AdjointState *a = m->adj;
     if (!a) return;
-    void *ptrs[] = {a->out_ptr, a->out_jump, a->out_dst, a->out_coef, a->je_ptr,  a->je_src, a->je_dst,
-                    a->je_coef, a->pe_ptr,   a->pe_row,  a->pe_col,   a->pe_unit, a->H};
+    void *ptrs[] = {a->out_ptr, a->out_jump, a->out_dst, a->out_coef, a->je_ptr, a->je_src,   a->je_dst, a->je_coef,
+                    a->pe_ptr,  a->pe_row,   a->pe_col,  a->pe_unit,  a->H,      a->a_pl,     a->b_pl,   a->c_slices};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (a->twin) qed_free(a->twin);
     delete a;
     m->adj = nullptr;
 }
@@ -289,9 +644,11 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         return QED_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->prec != QED_FP64)
+        return adjoint_split(m, rho0, n_steps, checkpoint_every, obs_diag, loss, grad_g, grad_zeta, grad_gamma, s);
     const int64_t D = m->D;
     const size_t DD = (size_t)(D * D);
-    const int64_t N = n_steps, k = checkpoint_every;
+    const int64_t N = n_steps, k = std::min<int64_t>(checkpoint_every, std::max<int64_t>(n_steps, 1));
     const int64_t n_ck = N > 0 ? (N - 1) / k + 1 : 0;
     const double dt = m->dt;
     Buffers B;
@@ -353,31 +710,7 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
             zgemm_ex(s, D, D, D, 1.0, m->U, D, true, T, D, false, 0.0, lam, D);
         }
     }
-    // G = L_exp(X, M): upper-right block of exp([[X, tau M], [0, X]])
-    if (a.n_g + a.n_zeta > 0) {
-        std::vector<double2> hM(DD);
-        QED_CUDA_TRY(cudaMemcpyAsync(hM.data(), Macc, DD * 16, cudaMemcpyDeviceToHost, s));
-        QED_CUDA_TRY(cudaStreamSynchronize(s));
-        double mnorm = 0.0;
-        for (int64_t cc = 0; cc < D; ++cc) {
-            double col = 0.0;
-            for (int64_t rr = 0; rr < D; ++rr) col += std::hypot(hM[(size_t)(rr * D + cc)].x, hM[(size_t)(rr * D + cc)].y);
-            mnorm = std::max(mnorm, col);
-        }
-        const double xnorm = dt * a.h_norm1;
-        double tau = 1.0;
-        if (mnorm > 0.0 && xnorm > 0.0) tau = std::ldexp(1.0, (int)std::floor(std::log2(xnorm / mnorm)));
-        double2 *blk = nullptr, *R = nullptr;
-        ADJ_TRY(B.get(&blk, 4 * DD));
-        ADJ_TRY(B.get(&R, 4 * DD));
-        block_kernel<<<blocks_for((int64_t)(4 * DD), 256), 256, 0, s>>>(D, a.H, dt, Macc, tau, blk);
-        count_launches(1);
-        ADJ_TRY(expm_pade13(s, 2 * D, blk, xnorm + tau * mnorm, R, m->err));
-        const int np = a.n_g + a.n_zeta;
-        param_grad_kernel<<<blocks_for(np, 128), 128, 0, s>>>(D, np, a.pe_ptr, a.pe_row, a.pe_col, a.pe_unit, R,
-                                                              2.0 * dt / tau, grad_g, a.n_g, grad_zeta);
-        count_launches(1);
-    }
+    ADJ_TRY(frechet_gradients(m, B, Macc, grad_g, grad_zeta, s));
     QED_CUDA_TRY(cudaStreamSynchronize(s));
     QED_CUDA_TRY(cudaGetLastError());
     return QED_OK;

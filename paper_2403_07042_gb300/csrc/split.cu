@@ -228,6 +228,22 @@ __global__ void import_kernel(int64_t D, int64_t Dp, const double2 *rho, float s
     pl[plane + m * 2 * Dp + Dp + n] = l;
 }
 
+// FP16 planes of GEMM1's B operand from the double-float state
+__global__ void planes_from_state_kernel(int64_t D, int64_t Dp, const float4 *st, float s, __half *pl) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = blockIdx.y;
+    if (n >= D) return;
+    const float4 v = st[m * D + n];
+    const int64_t plane = Dp * 2 * Dp;
+    __half h, l;
+    df_to_half2({v.x, v.y}, s, h, l);
+    pl[m * 2 * Dp + n] = h;
+    pl[plane + m * 2 * Dp + n] = l;
+    df_to_half2({v.z, v.w}, s, h, l);
+    pl[m * 2 * Dp + Dp + n] = h;
+    pl[plane + m * 2 * Dp + Dp + n] = l;
+}
+
 __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= D * D) return;
@@ -780,6 +796,16 @@ void split_batch_destroy(Batch *b) {
     if (!b) return;
     b->release();
     delete b;
+}
+
+float4 *split_state(qed_model *m) { return m->sp->rho_df[0]; }
+float4 *split_vbuf(qed_model *m) { return m->sp->rho_df[1]; }
+void split_dissipate_only(qed_model *m, cudaStream_t s) { launch_dissipate(m->sp->self, s); }
+void split_refresh_planes(qed_model *m, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    dim3 grid(blocks_for(m->D, 256), (unsigned)m->D);
+    planes_from_state_kernel<<<grid, 256, 0, s>>>(m->D, S.Dp, S.rho_df[0], (float)S.scale_rho, S.rho_pl);
+    count_launches(1);
 }
 
 void split_release(qed_model *m) {

@@ -19,6 +19,13 @@ void split_end(qed_model *m, double2 *rho, cudaStream_t s);              // inte
 int split_step_timed(qed_model *m, cudaStream_t s, std::string &label);
 void split_populations(qed_model *m, double *out, cudaStream_t s);      // out[k] = rho_kk
 
+// Access for the adjoint: the double-float state and V buffer (D x D float4), the Lindblad
+// pass alone (V buffer -> state + planes), the planes recomputed from the state.
+float4 *split_state(qed_model *m);
+float4 *split_vbuf(qed_model *m);
+void split_dissipate_only(qed_model *m, cudaStream_t s);
+void split_refresh_planes(qed_model *m, cudaStream_t s);
+
 // Many split-precision models stepped together: one grouped launch per phase.
 struct Batch;
 qed_status split_batch_create(qed_model *const *ms, int n, Batch **out);

@@ -133,3 +133,67 @@ def test_adjoint_argument_errors():
     rho = torch.zeros((36, 36), dtype=torch.complex128, device="cuda")
     with pytest.raises(qed.QedError):
         gm.adjoint(rho, 10, torch.zeros(36, dtype=torch.float64, device="cuda"), checkpoint_every=0)
+
+
+def _gpu_adjoint_prec(m, steps, w, k, precision, rho0=None, b=None):
+    b = b or oracle.enumerate_basis(m)
+    gm = qed.Model(m, precision=precision)
+    rho0 = oracle.initial_density(m, b) if rho0 is None else rho0
+    loss, gg, gz, gj = gm.adjoint(_cuda(rho0), steps, _cuda(w), checkpoint_every=k)
+    return float(loss), gg.cpu().numpy(), gz.cpu().numpy(), gj.cpu().numpy()
+
+
+# The split-precision adjoint carries each step's products to about 2^-22 = 2.4e-7 relative
+# (FP16 hi/lo pieces, FP32 accumulation) and the state as double-floats; over N <= 100 steps
+# the rounding errors add up to at most N * 2.4e-7 = 2.4e-5 of the largest gradient component
+# (measured: <= 3.1e-6), and to far less on the loss (measured: <= 2e-9).
+SPLIT_GRAD_RTOL = 2.4e-5
+SPLIT_LOSS_ATOL = 1e-7
+
+
+@pytest.mark.parametrize("nx,ny,steps,k", [(4, 4, 80, 16), (8, 8, 100, 30), (3, 3, 25, 100)])
+def test_split_adjoint_matches_oracle_lattice(nx, ny, steps, k):
+    """Several 128-row tiles at 8x8 (D = 129), ragged checkpoint segments, k > n_steps."""
+    m = W.lattice(nx, ny, seed=4, gamma=0.02, dt=0.1, n_steps=steps, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    ref = oracle.adjoint_gradients(m, w, n_steps=steps, basis=b)
+    got = _gpu_adjoint_prec(m, steps, w, k, "split_fp16x2", b=b)
+    errs = [np.abs(np.asarray(x) - y).max() / max(np.abs(y).max(), 1e-30) for x, y in zip(got[1:], ref[1:])]
+    print(f"split adjoint {nx}x{ny}: |dloss|={abs(got[0] - ref[0]):.2e} rel grad errs={errs}")
+    assert abs(got[0] - ref[0]) <= SPLIT_LOSS_ATOL
+    for x, y in zip(got[1:], ref[1:]):
+        assert _close(x, y, SPLIT_GRAD_RTOL)
+
+
+def test_split_adjoint_cavities_dephasing_large_observable():
+    """Observable weights up to 5 (the co-state is run at o / 8 and scaled back), random mixed
+    initial state, photon loss and extra-digit dephasing."""
+    m = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+             zeta=[0.006], dt=0.1)
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=11)
+    w = np.random.default_rng(2).uniform(-5, 5, b.dim)
+    ref = oracle.adjoint_gradients(m, w, n_steps=45, rho0=rho0, basis=b)
+    got = _gpu_adjoint_prec(m, 45, w, 10, "split_fp16x2", rho0=rho0, b=b)
+    assert abs(got[0] - ref[0]) <= 5 * SPLIT_LOSS_ATOL
+    for x, y in zip(got[1:], ref[1:]):
+        assert _close(x, y, SPLIT_GRAD_RTOL)
+
+
+def test_split_adjoint_autograd():
+    m = W.lattice(3, 3, seed=4, gamma=0.02, dt=0.1, n_steps=30, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    ref = oracle.adjoint_gradients(m, w, n_steps=30, basis=b)
+    g = torch.tensor(m["g"], dtype=torch.float64, requires_grad=True)
+    z = torch.tensor(m["zeta"], dtype=torch.float64, requires_grad=True)
+    gam = torch.tensor([x[2] for x in m["jumps"]], dtype=torch.float64, requires_grad=True)
+    loss = qed.qme_loss(g, z, gam, m, _cuda(oracle.initial_density(m, b)), 30, _cuda(w), 8,
+                        precision="split_fp16x2")
+    loss.backward()
+    assert abs(float(loss.detach()) - ref[0]) <= SPLIT_LOSS_ATOL
+    assert _close(g.grad.numpy(), ref[1], SPLIT_GRAD_RTOL)
+    assert _close(z.grad.numpy(), ref[2], SPLIT_GRAD_RTOL)
+    assert _close(gam.grad.numpy(), ref[3], SPLIT_GRAD_RTOL)
