@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include "gemm_tc.h"
+#include "pdl.h"
 #include "kernels.h"
 #include "model.h"
 
@@ -183,6 +184,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    // operands and outputs are shared with the neighbouring kernels of the step
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 0 && lane == 0) {
         // producer
@@ -457,7 +461,8 @@ bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_p
 template <int BN>
 void grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs, uint32_t *err,
                     cudaStream_t s) {
-    tc_gemm_grouped_kernel<BN><<<n_items, 128, tc_gemm_smem_bytes(BN), s>>>(items, jobs, segs, err);
+    launch_pdl(tc_gemm_grouped_kernel<BN>, dim3(n_items), dim3(128), tc_gemm_smem_bytes(BN), s, items, jobs, segs,
+               err);
 }
 
 void tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs, int bn,
@@ -499,9 +504,9 @@ void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) 
     dim3 grid((g.N + g.bn - 1) / g.bn, g.M / kTcBM, g.splits);
     count_launches(1);
     if (g.bn == 128)
-        tc_gemm_kernel<128><<<grid, 128, tc_gemm_smem_bytes(128), s>>>(g.a, g.b, p);
+        launch_pdl(tc_gemm_kernel<128>, grid, dim3(128), tc_gemm_smem_bytes(128), s, g.a, g.b, p);
     else
-        tc_gemm_kernel<256><<<grid, 128, tc_gemm_smem_bytes(256), s>>>(g.a, g.b, p);
+        launch_pdl(tc_gemm_kernel<256>, grid, dim3(128), tc_gemm_smem_bytes(256), s, g.a, g.b, p);
 }
 
 }  // namespace qed

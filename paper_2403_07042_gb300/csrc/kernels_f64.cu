@@ -107,6 +107,42 @@ __global__ void __launch_bounds__(64) zgemm_kernel(int64_t M, int64_t N, int64_t
     }
 }
 
+// Small products (fewer 32 x 32 tiles than SMs): FP64 issue is a few DFMA per clock per SM,
+// so the work is spread over as many SMs as possible instead of reused through shared
+// memory.  One warp per CTA computes 8 consecutive outputs of the row-major M x N result;
+// the 4 lanes of an output take every 4th k and are summed by shuffles.
+template <bool CONJ_A, bool CONJ_B>
+__global__ void __launch_bounds__(32) zgemm_small_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                         const double2 *__restrict__ A, int64_t lda,
+                                                         const double2 *__restrict__ B, int64_t ldb, double beta,
+                                                         double2 *__restrict__ C, int64_t ldc) {
+    const int lane = threadIdx.x, q = lane & 3;
+    const int64_t idx = (int64_t)blockIdx.x * 8 + (lane >> 2);
+    const bool valid = idx < M * N;
+    const int64_t m = valid ? idx / N : 0, n = valid ? idx % N : 0;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t k = q; k < K; k += 4) {
+        double2 a = CONJ_A ? A[k * lda + m] : A[m * lda + k];
+        double2 b = CONJ_B ? B[n * ldb + k] : B[k * ldb + n];
+        if (CONJ_A) a.y = -a.y;
+        if (CONJ_B) b.y = -b.y;
+        acc = cfma(a, b, acc);
+    }
+#pragma unroll
+    for (int off = 1; off < 4; off <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (!valid || q != 0) return;
+    double2 v = make_double2(alpha * acc.x, alpha * acc.y);
+    if (beta != 0.0) {
+        const double2 c = C[m * ldc + n];
+        v.x = fma(beta, c.x, v.x);
+        v.y = fma(beta, c.y, v.y);
+    }
+    C[m * ldc + n] = v;
+}
+
 __global__ void lincomb_kernel(int64_t D, double c0, const double2 *A, double c1, const double2 *B,
                                double c2, const double2 *C, double c3, double c4, double2 *Y) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,6 +332,24 @@ void zgemm_ex(cudaStream_t s, int64_t M, int64_t N, int64_t K, double alpha, con
               bool conj_a, const double2 *B, int64_t ldb, bool conj_b, double beta, double2 *C, int64_t ldc) {
     count_launches(1);
     dim3 grid(blocks_for(N, TN), blocks_for(M, TM));
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    if ((int64_t)grid.x * grid.y < sms) {
+        const unsigned nb = blocks_for(M * N, 8);
+        if (conj_a) {
+            if (conj_b)
+                zgemm_small_kernel<true, true><<<nb, 32, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+            else
+                zgemm_small_kernel<true, false><<<nb, 32, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        } else {
+            if (conj_b)
+                zgemm_small_kernel<false, true><<<nb, 32, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+            else
+                zgemm_small_kernel<false, false><<<nb, 32, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+        }
+        return;
+    }
     if (conj_a) {
         if (conj_b)
             zgemm_kernel<true, true><<<grid, 64, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);

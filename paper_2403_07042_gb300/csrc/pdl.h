@@ -1,0 +1,36 @@
+// Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled while
+// the previous kernel on the stream is still running.  Its CTAs do their private set-up
+// (shared-memory barriers, tensor-memory allocation, table reads), then pdl_wait() blocks
+// until the previous grid has completed and its writes are visible; only after that do they
+// read or write global data that other kernels of the step produce or consume.  Every
+// kernel launched this way calls pdl_wait() on all paths before its first such access, so
+// completion is transitive along the stream.  pdl_trigger() lets the next kernel start its
+// own set-up early.  On a normal launch both are no-ops.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+
+namespace qed {
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace qed

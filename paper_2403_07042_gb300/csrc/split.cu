@@ -27,6 +27,7 @@
 
 #include "gemm_tc.h"
 #include "kernels.h"
+#include "pdl.h"
 #include "split.h"
 
 namespace qed {
@@ -257,6 +258,8 @@ __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
 // per 32 x 32 tile of one instance.
 __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restrict__ tiles,
                                                        const InstDesc *__restrict__ descs) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float tre[32][33], tim[32][33];
     const TileItem it = tiles[blockIdx.x];
     const InstDesc &a = descs[it.inst];
@@ -299,6 +302,8 @@ __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restric
 // sum and the phase in double-float.  One block per 32 x 8 elements of one instance.
 __global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict__ tiles,
                                                      const InstDesc *__restrict__ descs) {
+    pdl_wait();
+    pdl_trigger();
     const TileItem it = tiles[blockIdx.x];
     const InstDesc &a = descs[it.inst];
     const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
@@ -324,6 +329,8 @@ __global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict_
 // to the double-float V.  Also writes the FP16 planes of rho for the next GEMM1.
 __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
                                                            const InstDesc *__restrict__ descs) {
+    pdl_wait();
+    pdl_trigger();
     const TileItem it = tiles[blockIdx.x];
     const InstDesc &a = descs[it.inst];
     const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
@@ -607,15 +614,15 @@ void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
     tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, err, s);
 }
 void launch_w_reduce(const Batch &b, cudaStream_t s) {
-    w_reduce_kernel<<<b.n_wtiles, dim3(32, 8), 0, s>>>(b.wtiles, b.desc);
+    launch_pdl(w_reduce_kernel, dim3(b.n_wtiles), dim3(32, 8), 0, s, b.wtiles, b.desc);
     count_launches(1);
 }
 void launch_form(const Batch &b, cudaStream_t s) {
-    form_v_kernel<<<b.n_etiles, dim3(32, 8), 0, s>>>(b.etiles, b.desc);
+    launch_pdl(form_v_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
     count_launches(1);
 }
 void launch_dissipate(const Batch &b, cudaStream_t s) {
-    dissipate_df_kernel<<<b.n_etiles, dim3(32, 8), 0, s>>>(b.etiles, b.desc);
+    launch_pdl(dissipate_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
     count_launches(1);
 }
 
