@@ -11,10 +11,12 @@
 // For a Hamiltonian parameter theta, dL/dtheta = 2 Re tr(dU/dtheta M) with
 // dU/dtheta = L_exp(X, -i dt dH/dtheta), X = -i dt H; since tr(L_exp(X, E) M) =
 // tr(L_exp(X, M) E), one Frechet derivative G = L_exp(X, M) serves every parameter:
-// dL/dtheta = 2 dt Im tr(G dH/dtheta).  G is the upper-right block of
-// exp([[X, M], [0, X]]) (Najfeld and Havel; Higham 2008, Sec. 10.6), computed with the same
-// Pade-13 routine as U.  rho is checkpointed every k steps and each segment recomputed
-// (storing its rho_n and V_n) while stepping the co-state back.
+// dL/dtheta = 2 dt Im tr(G dH/dtheta).  G comes from the Pade-13 approximant of exp and its
+// directional derivative, evaluated together (the upper-right block of
+// exp([[X, M], [0, X]]), Najfeld and Havel; Higham 2008, Sec. 10.6; Al-Mohy and Higham
+// 2009).  rho is checkpointed every k steps and each segment but the last recomputed
+// (storing its rho_n and V_n) while stepping the co-state back; the forward pass stores
+// the last segment directly, so k >= n_steps runs without recomputation.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -221,31 +223,14 @@ __global__ void __launch_bounds__(256) gamma_grad_kernel(int64_t D, const int32_
     if (t == 0) grad[j] += dt * part[0];
 }
 
-// B = [[X, tau M], [0, X]] with X = -i dt H (2D x 2D)
-__global__ void block_kernel(int64_t D, const double2 *H, double dt, const double2 *M, double tau, double2 *B) {
-    const int64_t W = 2 * D;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= W * W) return;
-    const int64_t r = idx / W, c = idx % W;
-    double2 v = make_double2(0.0, 0.0);
-    if ((r < D) == (c < D)) {
-        const double2 h = H[(r % D) * D + (c % D)];
-        v = make_double2(dt * h.y, -dt * h.x);
-    } else if (r < D && c >= D) {
-        const double2 x = M[r * D + (c - D)];
-        v = make_double2(tau * x.x, tau * x.y);
-    }
-    B[idx] = v;
-}
-
-// grad[p] = 2 dt Im sum_e unit_e G[col_e][row_e] / tau, G the upper-right block of R
+// grad[p] = 2 dt Im sum_e unit_e G[col_e][row_e], G = L_exp(X, M)
 __global__ void param_grad_kernel(int64_t D, int np, const int32_t *pe_ptr, const int32_t *pe_row,
-                                  const int32_t *pe_col, const double *pe_unit, const double2 *R, double scale,
+                                  const int32_t *pe_col, const double *pe_unit, const double2 *G, double scale,
                                   double *grad_g, int n_g, double *grad_zeta) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
     double s = 0.0;
-    for (int e = pe_ptr[p]; e < pe_ptr[p + 1]; ++e) s += pe_unit[e] * R[(int64_t)pe_col[e] * 2 * D + D + pe_row[e]].y;
+    for (int e = pe_ptr[p]; e < pe_ptr[p + 1]; ++e) s += pe_unit[e] * G[(int64_t)pe_col[e] * D + pe_row[e]].y;
     if (p < n_g)
         grad_g[p] = scale * s;
     else
@@ -475,8 +460,7 @@ qed_status make_twin(qed_model *m, cudaStream_t s) {
     return QED_OK;
 }
 
-// G = L_exp(X, M) as the upper-right block of exp([[X, tau M], [0, X]]) (tau a power of two
-// balancing the blocks' norms), contracted with dH/dtheta for every g and zeta.
+// G = L_exp(X, M), X = -i dt H, contracted with dH/dtheta for every g and zeta.
 qed_status frechet_gradients(qed_model *m, Buffers &B, const double2 *Macc, double *grad_g, double *grad_zeta,
                              cudaStream_t s) {
     AdjointState &a = *m->adj;
@@ -484,31 +468,26 @@ qed_status frechet_gradients(qed_model *m, Buffers &B, const double2 *Macc, doub
     const size_t DD = (size_t)(D * D);
     const double dt = m->dt;
     if (a.n_g + a.n_zeta > 0) {
-        std::vector<double2> hM(DD);
-        QED_CUDA_TRY(cudaMemcpyAsync(hM.data(), Macc, DD * 16, cudaMemcpyDeviceToHost, s));
-        QED_CUDA_TRY(cudaStreamSynchronize(s));
-        double mnorm = 0.0;
-        for (int64_t cc = 0; cc < D; ++cc) {
-            double col = 0.0;
-            for (int64_t rr = 0; rr < D; ++rr) col += std::hypot(hM[(size_t)(rr * D + cc)].x, hM[(size_t)(rr * D + cc)].y);
-            mnorm = std::max(mnorm, col);
-        }
-        const double xnorm = dt * a.h_norm1;
-        double tau = 1.0;
-        if (mnorm > 0.0 && xnorm > 0.0) tau = std::ldexp(1.0, (int)std::floor(std::log2(xnorm / mnorm)));
-        double2 *blk = nullptr, *R = nullptr;
-        ADJ_TRY(B.get(&blk, 4 * DD));
-        ADJ_TRY(B.get(&R, 4 * DD));
-        block_kernel<<<blocks_for((int64_t)(4 * DD), 256), 256, 0, s>>>(D, a.H, dt, Macc, tau, blk);
-        count_launches(1);
-        ADJ_TRY(expm_pade13(s, 2 * D, blk, xnorm + tau * mnorm, R, m->err));
+        double2 *X = nullptr, *R = nullptr, *G = nullptr;
+        ADJ_TRY(B.get(&X, DD));
+        ADJ_TRY(B.get(&R, DD));
+        ADJ_TRY(B.get(&G, DD));
+        scale_minus_i(s, D, dt, a.H, X);
+        ADJ_TRY(expm_frechet_pade13(s, D, X, Macc, dt * a.h_norm1, R, G, m->err));
         const int np = a.n_g + a.n_zeta;
-        param_grad_kernel<<<blocks_for(np, 128), 128, 0, s>>>(D, np, a.pe_ptr, a.pe_row, a.pe_col, a.pe_unit, R,
-                                                              2.0 * dt / tau, grad_g, a.n_g, grad_zeta);
+        param_grad_kernel<<<blocks_for(np, 128), 128, 0, s>>>(D, np, a.pe_ptr, a.pe_row, a.pe_col, a.pe_unit, G,
+                                                              2.0 * dt, grad_g, a.n_g, grad_zeta);
         count_launches(1);
     }
     QED_CUDA_TRY(cudaStreamSynchronize(s));
     QED_CUDA_TRY(cudaGetLastError());
+    uint32_t flags = 0;
+    QED_CUDA_TRY(cudaMemcpy(&flags, m->err, 4, cudaMemcpyDeviceToHost));
+    if (flags & kErrSingular) {
+        QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+        set_error("qed_adjoint: singular Pade denominator in the Frechet derivative");
+        return QED_ENUMERIC;
+    }
     return QED_OK;
 }
 
@@ -550,11 +529,18 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
     ADJ_TRY(B.get(&Macc, DD));
     ADJ_TRY(B.get(&r, (size_t)D));
     // forward with checkpoints of the double-float state
+    const int64_t last0 = (n_ck - 1) * k;  // the last segment is stored by the forward pass
     ADJ_TRY(split_begin(m, (const double2 *)rho0, s));
     for (int64_t n = 0; n < N; ++n) {
-        if (n % k == 0)
+        if (n % k == 0 && n < last0)
             QED_CUDA_TRY(cudaMemcpyAsync(ck + (size_t)(n / k) * DD, split_state(m), DD * 16, cudaMemcpyDeviceToDevice, s));
+        if (n >= last0)
+            QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + (size_t)(n - last0) * DD, split_state(m), DD * 16,
+                                         cudaMemcpyDeviceToDevice, s));
         split_step(m, s);
+        if (n >= last0)
+            QED_CUDA_TRY(cudaMemcpyAsync(seg_v + (size_t)(n - last0) * DD, split_vbuf(m), DD * 16,
+                                         cudaMemcpyDeviceToDevice, s));
     }
     loss_df_kernel<<<1, 256, 0, s>>>(D, split_state(m), obs_diag, loss);
     // co-state: lambda_N = diag(o) in the backward model's V buffer, kappa_N = J^+(lambda_N)
@@ -566,9 +552,11 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
     const dim3 rows(blocks_for(D, 256), (unsigned)D);
     for (int64_t c = n_ck - 1; c >= 0; --c) {
         const int64_t s0 = c * k, s1 = std::min(N, s0 + k);
-        QED_CUDA_TRY(cudaMemcpyAsync(split_state(m), ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
-        split_refresh_planes(m, s);
-        for (int64_t n = s0; n < s1; ++n) {
+        if (c < n_ck - 1) {
+            QED_CUDA_TRY(cudaMemcpyAsync(split_state(m), ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
+            split_refresh_planes(m, s);
+        }
+        for (int64_t n = s0; n < s1 && c < n_ck - 1; ++n) {
             QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + (size_t)(n - s0) * DD, split_state(m), DD * 16,
                                          cudaMemcpyDeviceToDevice, s));
             split_step(m, s);
@@ -665,13 +653,19 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
     ADJ_TRY(B.get(&T, DD));
     ADJ_TRY(B.get(&r, (size_t)D));
     // forward with checkpoints (FP64 step: V = (U rho) U^+, then Eq. 3)
+    const int64_t last0 = (n_ck - 1) * k;  // the last segment is stored by the forward pass
     QED_CUDA_TRY(cudaMemcpyAsync(rho, rho0, DD * 16, cudaMemcpyDeviceToDevice, s));
     for (int64_t n = 0; n < N; ++n) {
-        if (n % k == 0)
+        if (n % k == 0 && n < last0)
             QED_CUDA_TRY(cudaMemcpyAsync(ck + (size_t)(n / k) * DD, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
+        double2 *vn = m->work2;
+        if (n >= last0) {
+            QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + (size_t)(n - last0) * DD, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
+            vn = seg_v + (size_t)(n - last0) * DD;
+        }
         zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);
-        zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
-        dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, dt);
+        zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, vn, D);
+        dissipate_f64(s, D, vn, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, dt);
     }
     loss_kernel<<<1, 256, 0, s>>>(D, rho, obs_diag, loss);
     count_launches(1);
@@ -683,8 +677,9 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
     for (int64_t c = n_ck - 1; c >= 0; --c) {
         const int64_t s0 = c * k, s1 = std::min(N, s0 + k);
         // recompute the segment, storing rho_n and V_n
-        QED_CUDA_TRY(cudaMemcpyAsync(rho, ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
-        for (int64_t n = s0; n < s1; ++n) {
+        if (c < n_ck - 1)
+            QED_CUDA_TRY(cudaMemcpyAsync(rho, ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
+        for (int64_t n = s0; n < s1 && c < n_ck - 1; ++n) {
             double2 *vn = seg_v + (size_t)(n - s0) * DD;
             QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + (size_t)(n - s0) * DD, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
             zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);

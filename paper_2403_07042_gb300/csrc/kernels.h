@@ -37,6 +37,16 @@ void pade_augment(cudaStream_t s, int64_t D, const double2 *Up, const double2 *V
 // half holds Q^-1 P.  Sets kErrSingular in *err if a pivot is exactly zero.
 void gauss_jordan(cudaStream_t s, int64_t D, double2 *aug, uint32_t *err);
 
+// The same on a D x W matrix [Q | B_1 | B_2 | ...]: afterwards columns D.. hold Q^-1 B_i.
+void gauss_jordan_w(cudaStream_t s, int64_t D, int64_t W, double2 *aug, uint32_t *err);
+
+// aug (D x 4D) = [V - U | V + U | dV + dU | dV - dU]
+void frechet_augment(cudaStream_t s, int64_t D, const double2 *Up, const double2 *Vp, const double2 *dUp,
+                     const double2 *dVp, double2 *aug);
+
+// out (D x D) = columns [c0, c0 + D) of the D x W matrix aug
+void take_block(cudaStream_t s, int64_t D, int64_t W, int64_t c0, const double2 *aug, double2 *out);
+
 // Copy the right half of aug (D x 2D) into R (D x D).
 void take_right_half(cudaStream_t s, int64_t D, const double2 *aug, double2 *R);
 
@@ -54,6 +64,10 @@ void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *we
 qed_status propagator(cudaStream_t s, int64_t D, double dt, const double2 *H, double h_norm1, double2 *U,
                       uint32_t *err);
 qed_status expm_pade13(cudaStream_t s, int64_t D, const double2 *X, double xnorm, double2 *R, uint32_t *err);
+// R = exp(X) and L = L_exp(X, E), the Frechet derivative of exp at X in the direction E
+// (general complex X with 1-norm xnorm, any E); same Pade-13 scaling and squaring.
+qed_status expm_frechet_pade13(cudaStream_t s, int64_t D, const double2 *X, const double2 *E, double xnorm,
+                               double2 *R, double2 *L, uint32_t *err);
 
 // rho <- (rho + rho^+) / (2 tr rho); flags non-finite traces in *err.
 void renormalise(cudaStream_t s, int64_t D, double2 *rho, double *scratch, uint32_t *err);

@@ -172,12 +172,33 @@ __global__ void pade_augment_kernel(int64_t D, const double2 *Up, const double2 
     aug[r * 2 * D + D + c] = make_double2(v.x + u.x, v.y + u.y);
 }
 
+// aug (D x 4D) = [V - U | V + U | dV + dU | dV - dU]
+__global__ void frechet_augment_kernel(int64_t D, const double2 *Up, const double2 *Vp, const double2 *dUp,
+                                       const double2 *dVp, double2 *aug) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * D) return;
+    int64_t r = idx / D, c = idx % D;
+    const double2 u = Up[idx], v = Vp[idx], du = dUp[idx], dv = dVp[idx];
+    double2 *row = aug + r * 4 * D;
+    row[c] = make_double2(v.x - u.x, v.y - u.y);
+    row[D + c] = make_double2(v.x + u.x, v.y + u.y);
+    row[2 * D + c] = make_double2(dv.x + du.x, dv.y + du.y);
+    row[3 * D + c] = make_double2(dv.x - du.x, dv.y - du.y);
+}
+
+// out (D x D) = columns [c0, c0 + D) of the D x W matrix aug
+__global__ void take_block_kernel(int64_t D, int64_t W, int64_t c0, const double2 *aug, double2 *out) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= D * D) return;
+    out[idx] = aug[(idx / D) * W + c0 + idx % D];
+}
+
 // One block: pivot search in column k (rows >= k), row swap, scaling of row k.
-__global__ void __launch_bounds__(1024) gj_pivot_kernel(int64_t D, int64_t k, double2 *aug, uint32_t *err) {
+__global__ void __launch_bounds__(1024) gj_pivot_kernel(int64_t D, int64_t W, int64_t k, double2 *aug,
+                                                        uint32_t *err) {
     __shared__ double best[1024];
     __shared__ int64_t arg[1024];
     const int t = threadIdx.x;
-    const int64_t W = 2 * D;
     double b = -1.0;
     int64_t a = k;
     for (int64_t i = k + t; i < D; i += blockDim.x) {
@@ -222,9 +243,8 @@ __global__ void __launch_bounds__(1024) gj_pivot_kernel(int64_t D, int64_t k, do
 }
 
 // rows i != k: row_i -= aug[i][k] * row_k, for columns j > k.
-__global__ void gj_eliminate_kernel(int64_t D, int64_t k, double2 *aug, const uint32_t *err) {
+__global__ void gj_eliminate_kernel(int64_t D, int64_t W, int64_t k, double2 *aug, const uint32_t *err) {
     if (*err & kErrSingular) return;
-    const int64_t W = 2 * D;
     const int64_t i = blockIdx.y;
     const int64_t j = k + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == k || j >= W) return;
@@ -384,16 +404,29 @@ void pade_augment(cudaStream_t s, int64_t D, const double2 *Up, const double2 *V
     pade_augment_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, Up, Vp, aug);
 }
 
-void gauss_jordan(cudaStream_t s, int64_t D, double2 *aug, uint32_t *err) {
+void gauss_jordan(cudaStream_t s, int64_t D, double2 *aug, uint32_t *err) { gauss_jordan_w(s, D, 2 * D, aug, err); }
+
+void gauss_jordan_w(cudaStream_t s, int64_t D, int64_t W, double2 *aug, uint32_t *err) {
     count_launches(2 * D);
     for (int64_t k = 0; k < D; ++k) {
-        gj_pivot_kernel<<<1, 1024, 0, s>>>(D, k, aug, err);
-        int64_t cols = 2 * D - k - 1;
+        gj_pivot_kernel<<<1, 1024, 0, s>>>(D, W, k, aug, err);
+        int64_t cols = W - k - 1;
         if (cols > 0) {
             dim3 grid(blocks_for(cols, 256), (unsigned)D);
-            gj_eliminate_kernel<<<grid, 256, 0, s>>>(D, k, aug, err);
+            gj_eliminate_kernel<<<grid, 256, 0, s>>>(D, W, k, aug, err);
         }
     }
+}
+
+void frechet_augment(cudaStream_t s, int64_t D, const double2 *Up, const double2 *Vp, const double2 *dUp,
+                     const double2 *dVp, double2 *aug) {
+    count_launches(1);
+    frechet_augment_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, Up, Vp, dUp, dVp, aug);
+}
+
+void take_block(cudaStream_t s, int64_t D, int64_t W, int64_t c0, const double2 *aug, double2 *out) {
+    count_launches(1);
+    take_block_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, W, c0, aug, out);
 }
 
 void take_right_half(cudaStream_t s, int64_t D, const double2 *aug, double2 *R) {

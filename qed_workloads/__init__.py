@@ -179,13 +179,15 @@ def batched_chains(n_instances=512, seed=0, dim_lo=32, dim_hi=1024, n_steps=1000
 
 
 def adjoint_lattice(length=24, width=24, seed=0, gamma=1e-3, dt=0.1, n_steps=1000,
-                    checkpoint_every=50):
+                    checkpoint_every=None):
     """24 x 24 lattice with per-cavity g and per-bond zeta; the photon starts in the
-    corner cavity (0, 0), and the loss is the photon + atom population there."""
+    corner cavity (0, 0), and the loss is the photon + atom population there.  By default
+    every state of the trajectory is kept for the backward pass (checkpoint_every =
+    n_steps: 2 x 1000 x 21 MB = 42 GB of device memory) and nothing is recomputed."""
     m = lattice(length, width, gamma=gamma, dt=dt, n_steps=n_steps, record_every=n_steps,
                 start=(0, 0), seed=seed)
     m["name"] = f"adjoint_lattice_{length}x{width}"
-    m["checkpoint_every"] = checkpoint_every
+    m["checkpoint_every"] = n_steps if checkpoint_every is None else checkpoint_every
     m["loss_states"] = {"photons": [0], "atoms": [0]}
     return m
 
