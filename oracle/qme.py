@@ -521,6 +521,25 @@ def full_product_rows(model):
 
 
 # ------------------------------------------------------------------ gradients
+def _trace_dissipator(lam, V, A):
+    """tr(lam D_A(V)) with D_A(V) = A V A^+ - 1/2 (A^+A V + V A^+A) (Eq. 3, one jump, unit
+    rate), for a sparse A without forming D x D intermediates:
+      tr(lam A V A^+) = sum over k, l in R of lam[l, k] (A V A^+)[k, l], R the rows where A
+      has entries (A V A^+ vanishes outside R x R);
+      tr(lam (K V + V K)) = sum over the entries K[m, j] of K[m, j] ((V lam)[j, m] +
+      (lam V)[j, m]), K = A^+A."""
+    rows = np.flatnonzero(np.diff(A.indptr))
+    if len(rows) == 0:
+        return 0.0
+    Ar = A[rows, :]
+    S = (Ar @ (Ar @ V).conj().T).conj().T          # (A V A^+) on R x R
+    sandwich = np.sum(lam[np.ix_(rows, rows)].T * S)
+    K = (A.conj().T @ A).tocoo()
+    vl = np.einsum("ei,ie->e", V[K.col, :], lam[:, K.row])
+    lv = np.einsum("ei,ie->e", lam[K.col, :], V[:, K.row])
+    return sandwich - 0.5 * np.sum(K.data * (vl + lv))
+
+
 def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
     """Discrete adjoint of L = tr(diag(obs) rho_N) through the map of `step`.
 
@@ -551,8 +570,7 @@ def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
     for n in reversed(range(n_steps)):
         V = U @ rhos[n] @ U.conj().T
         for j, (gamma, A) in enumerate(jumps):
-            Dj = lindblad(V, [(1.0, A)])
-            grad_gamma[j] += dt * np.real(np.trace(lam_next @ Dj))
+            grad_gamma[j] += dt * np.real(_trace_dissipator(lam_next, V, A))
         lam_prime = lam_next + dt * lindblad_adjoint(lam_next, jumps)
         M += rhos[n] @ U.conj().T @ lam_prime
         lam_next = U.conj().T @ lam_prime @ U

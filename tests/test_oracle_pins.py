@@ -392,3 +392,29 @@ def test_adjoint_matches_central_differences():
 
     fd = stencil(with_rate)
     assert abs(gga[j] - fd) <= 1e-6 * abs(fd) + 1e-10
+
+
+def test_rate_gradients_all_jump_kinds_match_central_differences():
+    """dL/dgamma_j for photon loss, atom decay and dephasing of an extra two-level degree of
+    freedom, from a random mixed state, against the fourth-order central stencil."""
+    m = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+             zeta=[0.006], dt=0.1)
+    m["jumps"] = list(m["jumps"]) + [(1, 0, 0.01)]
+    b = oracle.enumerate_basis(m)
+    kinds = sorted({int(k) for k, _, _ in m["jumps"]})
+    assert kinds == [0, 1, 2]
+    rho0 = W.random_density(b.dim, seed=5)
+    w = np.random.default_rng(3).uniform(-1, 1, b.dim)
+    _, _, _, gga = oracle.adjoint_gradients(m, w, n_steps=30, rho0=rho0, basis=b)
+    h = 1e-3
+
+    def loss(jumps):
+        rho = oracle.evolve(dict(m, jumps=jumps), n_steps=30, rho0=rho0, basis=b, return_records=False)
+        return float(np.sum(w * np.real(np.diag(rho))))
+
+    for j in range(len(m["jumps"])):
+        def f(d):
+            return loss([(k, s, g + (d if q == j else 0.0)) for q, (k, s, g) in enumerate(m["jumps"])])
+        fd = (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+        assert abs(gga[j] - fd) <= 1e-6 * abs(fd) + 1e-10, (j, gga[j], fd)
