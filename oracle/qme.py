@@ -254,6 +254,22 @@ def hamiltonian(model, basis=None, param=None):
     return H
 
 
+def hamiltonian_derivative_entries(model, basis=None):
+    """{param: [(row, col, unit_amplitude), ...]}: the entries of dH/dparam for every
+    parameter at once (the same terms as hamiltonian(model, basis, param), collected in one
+    pass over the basis)."""
+    basis = basis or enumerate_basis(model)
+    ent = {}
+    for k in range(basis.dim):
+        for t, unit, coef, p in _apply_terms(model, basis, basis.digits[k]):
+            if p is None:
+                continue
+            j = basis.find(t)
+            if j >= 0:
+                ent.setdefault(p, []).append((j, k, unit))
+    return ent
+
+
 def jump_operator(model, basis, kind, site):
     """A_j projected on the basis (PAP) as a scipy.sparse CSR matrix."""
     lay = basis.layout
@@ -580,10 +596,14 @@ def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
     F = np.where(same, -1j * dt * f[:, None], (f[:, None] - f[None, :]) / np.where(same, 1.0, dl))
     Mt = Q.conj().T @ M @ Q
     K = Q @ (F.T * Mt) @ Q.conj().T   # tr(dU M) = tr(dH K)
-    grad_g = np.array([2.0 * np.real(np.sum(hamiltonian(model, basis, ("g", a)) * K.T))
-                       for a in range(len(model["g"]))])
-    grad_zeta = np.array([2.0 * np.real(np.sum(hamiltonian(model, basis, ("zeta", b)) * K.T))
-                          for b in range(len(model["zeta"]))])
+    # tr(dH/dtheta K) = sum over the entries (j, k, u) of dH/dtheta of u K[k, j]
+    ent = hamiltonian_derivative_entries(model, basis)
+
+    def contract(p):
+        return 2.0 * np.real(sum(u * K[k, j] for j, k, u in ent.get(p, [])))
+
+    grad_g = np.array([contract(("g", a)) for a in range(len(model["g"]))])
+    grad_zeta = np.array([contract(("zeta", b)) for b in range(len(model["zeta"]))])
     return loss, grad_g, grad_zeta, grad_gamma
 
 

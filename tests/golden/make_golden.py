@@ -2,6 +2,7 @@
 
 Calls only the FP64 oracle (and the seeded workload module).  Usage:
     python tests/golden/make_golden.py hb_shaped_d512
+    python tests/golden/make_golden.py adjoint_lattice_24x24_d1153
 """
 import os
 import sys
@@ -41,6 +42,19 @@ def lattice_32x32_d2049():
     np.savez_compressed(os.path.join(HERE, "lattice_32x32_d2049_oracle.npz"), records=rec,
                         rho_rows=np.array(rows), rho_sample=rho[rows], trace=np.trace(rho).real,
                         seconds=time.time() - t0)
+
+
+def adjoint_lattice_24x24_d1153():
+    """The 24 x 24 adjoint workload (dim 1153, 1000 steps of dt 0.1): the loss (photon +
+    atom population of the corner cavity) and its gradients with respect to all 576 g,
+    1104 zeta and 576 leak rates, from the oracle's discrete adjoint."""
+    m = W.adjoint_lattice()
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, **m["loss_states"])
+    t0 = time.time()
+    loss, gg, gz, gj = oracle.adjoint_gradients(m, w, basis=b)
+    np.savez_compressed(os.path.join(HERE, "adjoint_lattice_24x24_d1153_oracle.npz"), loss=loss, grad_g=gg,
+                        grad_zeta=gz, grad_gamma=gj, seconds=time.time() - t0)
 
 
 if __name__ == "__main__":
