@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -47,8 +48,16 @@ struct InstDesc {
     const float2 *damp;
     const int32_t *in_ptr, *in_jump, *in_src;
     const float2 *coef;
+    const int4 *in_tab;     // [D][kInMax] {jump, src, coef hi, coef lo} or null (use the lists)
     __half *rho_pl, *w_pl;
 };
+
+// Rows with at most kInMax incoming jump entries use a padded table (one vector load per
+// entry, all gathers in flight together) instead of the two-pointer merge of the lists.
+constexpr int kInMax = 4;
+constexpr int kNoJump = 0x7fffffff;
+// Split-K slices the element-wise kernels sum (the plan caps them at 4).
+constexpr int kMaxSlices = 4;
 
 // 32 x 32 tiles of W (w_reduce) or 32 x 8 element blocks (form_v, dissipate) of one instance
 struct TileItem {
@@ -94,6 +103,7 @@ struct SplitState {
     float4 *phase_df = nullptr;              // D: P_k as {re_hi, re_lo, im_hi, im_lo}
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
     float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
+    int4 *in_tab = nullptr;                  // padded incoming table (rows with <= kInMax entries)
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
 };
 
@@ -258,11 +268,13 @@ __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
 // per 32 x 32 tile of one instance.
 __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restrict__ tiles,
                                                        const InstDesc *__restrict__ descs) {
+    __shared__ float tre[32][33], tim[32][33];
+    // the work item and the descriptor are written once at set-up: read them while the
+    // previous kernel finishes
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc a = descs[it.inst];
     pdl_wait();
     pdl_trigger();
-    __shared__ float tre[32][33], tim[32][33];
-    const TileItem it = tiles[blockIdx.x];
-    const InstDesc &a = descs[it.inst];
     const int64_t Dp = a.Dp;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     const int64_t k0 = (int64_t)it.by * 32, l0 = (int64_t)it.bx * 32;
@@ -302,25 +314,38 @@ __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restric
 // sum and the phase in double-float.  One block per 32 x 8 elements of one instance.
 __global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict__ tiles,
                                                      const InstDesc *__restrict__ descs) {
-    pdl_wait();
-    pdl_trigger();
+    // set-up tables and the constant phases are read while the previous kernel finishes
     const TileItem it = tiles[blockIdx.x];
-    const InstDesc &a = descs[it.inst];
+    const InstDesc a = descs[it.inst];
     const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
     const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
-    if (m >= a.D || n >= a.D) return;
+    const bool inside = m < a.D && n < a.D;
+    const cdf pm = load_cdf(a.phase[inside ? m : 0]), pn = load_cdf(a.phase[inside ? n : 0]);
+    pdl_wait();
+    pdl_trigger();
+    if (!inside) return;
     const int64_t Dp = a.Dp, stride = Dp * 2 * Dp;
-    float xr = 0.f, xi = 0.f;
-    for (int s = 0; s < a.splits2; ++s) {
-        xr += a.part[s * stride + m * 2 * Dp + n];
-        xi += a.part[s * stride + m * 2 * Dp + Dp + n];
+    const int splits = a.splits2;
+    // all loads issued before the first use
+    float pr[kMaxSlices], pi[kMaxSlices];
+#pragma unroll
+    for (int s = 0; s < kMaxSlices; ++s) {
+        pr[s] = s < splits ? __ldcg(a.part + s * stride + m * 2 * Dp + n) : 0.f;
+        pi[s] = s < splits ? __ldcg(a.part + s * stride + m * 2 * Dp + Dp + n) : 0.f;
     }
-    const float ir = a.w32[m * Dp + n] + a.wt32[m * Dp + n] + xr * a.inv_x;
-    const float ii = a.w32[Dp * Dp + m * Dp + n] - a.wt32[Dp * Dp + m * Dp + n] + xi * a.inv_x;
+    const float wr = a.w32[m * Dp + n], wtr = a.wt32[m * Dp + n];
+    const float wi = a.w32[Dp * Dp + m * Dp + n], wti = a.wt32[Dp * Dp + m * Dp + n];
     cdf r = load_cdf(a.rho[m * a.D + n]);
+    float xr = pr[0], xi = pi[0];
+#pragma unroll
+    for (int s = 1; s < kMaxSlices; ++s) {
+        xr += pr[s];
+        xi += pi[s];
+    }
+    const float ir = wr + wtr + xr * a.inv_x;
+    const float ii = wi - wti + xi * a.inv_x;
     r.re = df_add_f(r.re, ir);
     r.im = df_add_f(r.im, ii);
-    const cdf pm = load_cdf(a.phase[m]), pn = load_cdf(a.phase[n]);
     a.V[m * a.D + n] = store_cdf(cdf_mul(cdf_mul_conj(pm, pn), r));
 }
 
@@ -329,21 +354,62 @@ __global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict_
 // to the double-float V.  Also writes the FP16 planes of rho for the next GEMM1.
 __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
                                                            const InstDesc *__restrict__ descs) {
-    pdl_wait();
-    pdl_trigger();
+    // set-up tables (damping, padded jump rows) are read while the previous kernel finishes
     const TileItem it = tiles[blockIdx.x];
-    const InstDesc &a = descs[it.inst];
+    const InstDesc a = descs[it.inst];
+    const int64_t D = a.D;
     const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
     const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
-    if (m >= a.D || n >= a.D) return;
-    const int64_t D = a.D;
+    const bool inside = m < D && n < D;
+    const int64_t mc = inside ? m : 0, nc = inside ? n : 0;
+    const float2 dm = a.damp[mc], dn = a.damp[nc];
+    int4 em[kInMax], en[kInMax];
+    if (a.in_tab) {
+#pragma unroll
+        for (int i = 0; i < kInMax; ++i) {
+            em[i] = a.in_tab[mc * kInMax + i];
+            en[i] = a.in_tab[nc * kInMax + i];
+        }
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (!inside) return;
     const cdf v = load_cdf(a.V[m * D + n]);
-    const float2 dm = a.damp[m], dn = a.damp[n];
     const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
     float gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
     float gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
-    int p = a.in_ptr[m], pe = a.in_ptr[m + 1];
-    int q = a.in_ptr[n], qe = a.in_ptr[n + 1];
+    if (a.in_tab) {
+        // padded rows: pairs of equal jumps, every gather issued before the first use
+        float4 u[kInMax];
+        float2 cq[kInMax];
+        bool hit[kInMax];
+#pragma unroll
+        for (int i = 0; i < kInMax; ++i) {
+            int src = 0;
+            float2 c2 = make_float2(0.f, 0.f);
+            bool h = false;
+#pragma unroll
+            for (int j = 0; j < kInMax; ++j)
+                if (en[j].x == em[i].x) {
+                    h = true;
+                    src = en[j].y;
+                    c2 = make_float2(__int_as_float(en[j].z), __int_as_float(en[j].w));
+                }
+            hit[i] = h && em[i].x != kNoJump;
+            cq[i] = c2;
+            u[i] = hit[i] ? a.V[(int64_t)em[i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kInMax; ++i) {
+            if (!hit[i]) continue;
+            const df c = df_mul({__int_as_float(em[i].z), __int_as_float(em[i].w)}, {cq[i].x, cq[i].y});
+            const float ur = u[i].x + u[i].y, ui = u[i].z + u[i].w;
+            gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
+            gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
+        }
+    }
+    int p = a.in_tab ? 0 : a.in_ptr[m], pe = a.in_tab ? 0 : a.in_ptr[m + 1];
+    int q = a.in_tab ? 0 : a.in_ptr[n], qe = a.in_tab ? 0 : a.in_ptr[n + 1];
     while (p < pe && q < qe) {  // jumps present in both incoming lists
         const int jp = a.in_jump[p], jq = a.in_jump[q];
         if (jp < jq) {
@@ -506,6 +572,10 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.Dp = S.Dp;
         d.splits1 = single ? S.g1.splits : 1;  // split-K slices summed by w_reduce
         d.splits2 = single ? S.g2.splits : 1;  // and by form_v
+        if (d.splits1 > kMaxSlices || d.splits2 > kMaxSlices) {
+            set_error("split step: more split-K slices than the element-wise kernels sum");
+            return QED_EINVAL;
+        }
         d.inv_w = (float)(1.0 / (S.scale_delta * S.scale_rho));
         d.s_w = (float)S.scale_w;
         d.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
@@ -521,6 +591,7 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.in_jump = m->in_jump;
         d.in_src = m->in_src;
         d.coef = S.coef_df;
+        d.in_tab = S.in_tab;
         d.rho_pl = S.rho_pl;
         d.w_pl = S.w_pl;
         // a model on its own keeps its plans; in a batch every product runs unsplit with the
@@ -687,6 +758,29 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         for (int64_t e = 0; e < m->n_in; ++e) cdf_[(size_t)e] = split_f(std::sqrt(m->dt) * coef[(size_t)e]);
         SPLIT_TRY(alloc(&S.coef_df, cdf_.size()));
         QED_CUDA_TRY(cudaMemcpy(S.coef_df, cdf_.data(), cdf_.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        // the padded table when no row has more than kInMax incoming entries
+        std::vector<int32_t> ptr((size_t)D + 1), jmp((size_t)std::max<int64_t>(m->n_in, 1)),
+            src((size_t)std::max<int64_t>(m->n_in, 1));
+        QED_CUDA_TRY(cudaMemcpy(ptr.data(), m->in_ptr, ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (m->n_in > 0) {
+            QED_CUDA_TRY(cudaMemcpy(jmp.data(), m->in_jump, (size_t)m->n_in * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            QED_CUDA_TRY(cudaMemcpy(src.data(), m->in_src, (size_t)m->n_in * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        int32_t widest = 0;
+        for (int64_t k = 0; k < D; ++k) widest = std::max(widest, ptr[(size_t)k + 1] - ptr[(size_t)k]);
+        if (widest <= kInMax) {
+            std::vector<int4> tab((size_t)D * kInMax, make_int4(kNoJump, 0, 0, 0));
+            for (int64_t k = 0; k < D; ++k)
+                for (int32_t e = ptr[(size_t)k]; e < ptr[(size_t)k + 1]; ++e) {
+                    const float2 c = cdf_[(size_t)e];
+                    int f_hi = 0, f_lo = 0;
+                    std::memcpy(&f_hi, &c.x, 4);
+                    std::memcpy(&f_lo, &c.y, 4);
+                    tab[(size_t)(k * kInMax + (e - ptr[(size_t)k]))] = make_int4(jmp[(size_t)e], src[(size_t)e], f_hi, f_lo);
+                }
+            SPLIT_TRY(alloc(&S.in_tab, tab.size()));
+            QED_CUDA_TRY(cudaMemcpy(S.in_tab, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        }
     }
     SplitState &S = *m->sp;
     // Delta into work1, its scales from a host copy, then the constant planes
@@ -820,7 +914,7 @@ void split_release(qed_model *m) {
     SplitState &S = *m->sp;
     S.self.release();
     void *ptrs[] = {S.a1,        S.b2,        S.rho_pl,   S.w_pl,    S.w32,     S.wt32,
-                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df};
+                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df, S.in_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m->sp;
