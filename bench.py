@@ -321,6 +321,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one GEMM1 launch (ncu, warm L2)
+GEMM1_DRAM_BYTES_D512 = 256
+
+
 def make_roofline(kern, D, precision):
     peaks, src = measured_peaks()
     if not kern:
@@ -341,8 +345,11 @@ def make_roofline(kern, D, precision):
         flops = 2.0 * (2 * Dp) * Dp * (2 * Dp) * segs
         achieved = flops / (ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
+        # DRAM bytes per launch from one ncu capture of this kernel in the steady state of the
+        # dim-512 step (profiles/tc_gemm_hb_shaped_d512_full.md): the operands stay in L2
+        traffic = GEMM1_DRAM_BYTES_D512 if (name.startswith("gemm1") and D == 512) else None
         return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)"}
     # element-wise update: bytes per element
     bytes_ = 56.0 * D * D
