@@ -371,6 +371,24 @@ def step(rho, U, jumps, dt):
     return V + dt * lindblad(V, jumps)
 
 
+def lindblad_midpoint(X, jumps, tau):
+    """tau of the Lindblad flow dX/dt = L(X) (Eq. 3) by the explicit midpoint rule,
+    X + tau L(X + tau/2 L(X)); for the linear L this is X + tau L X + tau^2/2 L^2 X."""
+    return X + tau * lindblad(X + 0.5 * tau * lindblad(X, jumps), jumps)
+
+
+def step_strang(rho, U, jumps, dt):
+    """One symmetric step of the two stages (Lindblad term, unitary evolution): half a
+    Lindblad step, U . U^+, half a Lindblad step, the halves by the explicit midpoint
+    rule.  Second order in dt."""
+    X = lindblad_midpoint(rho, jumps, 0.5 * dt)
+    V = U @ X @ U.conj().T
+    return lindblad_midpoint(V, jumps, 0.5 * dt)
+
+
+STEPS = {"lie": step, "strang": step_strang}
+
+
 def observable_weights(model, basis):
     """Diagonal observables: trace, photon number per cavity, atom excitation per atom,
     extra digit per extra DOF (in that order)."""
@@ -394,8 +412,10 @@ def observables(rho, weights, obs_ids):
 
 
 def evolve(model, rho0=None, n_steps=None, record_every=None, obs_ids=None, U=None,
-           basis=None, return_records=True):
-    """Integrate n_steps; record observables at steps 0, r, 2r, ... (<= n_steps)."""
+           basis=None, return_records=True, scheme="lie"):
+    """Integrate n_steps with the step of `scheme` ('lie' or 'strang'); record observables
+    at steps 0, r, 2r, ... (<= n_steps)."""
+    advance = STEPS[scheme]
     basis = basis or enumerate_basis(model)
     H = hamiltonian(model, basis)
     dt = model["dt"]
@@ -411,7 +431,7 @@ def evolve(model, rho0=None, n_steps=None, record_every=None, obs_ids=None, U=No
         if n % r == 0:
             records.append(observables(rho, W, obs_ids))
         if n < n_steps:
-            rho = step(rho, U, jumps, dt)
+            rho = advance(rho, U, jumps, dt)
     if return_records:
         return rho, np.array(records)
     return rho

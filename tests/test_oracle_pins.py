@@ -418,3 +418,59 @@ def test_rate_gradients_all_jump_kinds_match_central_differences():
             return loss([(k, s, g + (d if q == j else 0.0)) for q, (k, s, g) in enumerate(m["jumps"])])
         fd = (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
         assert abs(gga[j] - fd) <= 1e-6 * abs(fd) + 1e-10, (j, gga[j], fd)
+
+
+# ---------------------------------------------------------------- Strang scheme
+def test_strang_second_order_convergence_to_continuum():
+    """The symmetric scheme (midpoint half Lindblad steps around U) converges to exp(L t)
+    rho_0 at second order in dt: halving dt divides the error by ~4."""
+    m = W.jch_two_cavities(gamma=0.05)
+    b = oracle.enumerate_basis(m)
+    t = 20.0
+    exact = oracle.continuum(m, t, basis=b)
+    errs = []
+    for dt in (0.2, 0.1, 0.05):
+        mm = dict(m, dt=dt, n_steps=int(round(t / dt)))
+        rho = oracle.evolve(mm, basis=b, return_records=False, scheme="strang")
+        errs.append(np.abs(rho - exact).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.6 <= e1 / e2 <= 4.4, errs
+    # and it is far closer to the continuum than the first-order step at the same dt
+    lie = oracle.evolve(dict(m, dt=0.1, n_steps=200), basis=b, return_records=False)
+    assert errs[1] < 0.05 * np.abs(lie - exact).max()
+
+
+def test_strang_discrete_photon_decay():
+    """H = omega a^+a, A = a: L^+(a^+a) = -gamma a^+a, so each midpoint half step multiplies
+    <n> by 1 - gamma dt/2 + (gamma dt/2)^2/2 and U keeps it: <n>_k = that factor^(2k) <n>_0."""
+    gamma, dt, steps = 0.02, 0.1, 500
+    m = W._model(n_cavities=1, atoms_per_cavity=[0], n_max=[6], jumps=[(0, 0, gamma)],
+                 dt=dt, n_steps=steps, init={"photons": {0: 4}})
+    b = oracle.enumerate_basis(m)
+    rng = np.random.default_rng(1)
+    psi = rng.standard_normal(7) + 1j * rng.standard_normal(7)
+    psi /= np.linalg.norm(psi)
+    rho0 = np.outer(psi, psi.conj())
+    _, rec = oracle.evolve(m, rho0=rho0, basis=b, obs_ids=[b.dim + 1], scheme="strang")
+    n0 = float(np.real(np.sum(np.arange(7) * np.diag(rho0))))
+    h = 0.5 * gamma * dt
+    want = n0 * (1 - h + 0.5 * h * h) ** (2 * np.arange(steps + 1))
+    assert np.abs(rec[:, 0] - want).max() < 1e-13
+    # second order: within (gamma dt)^2 gamma t / 24 of exp(-gamma t) (plus rounding)
+    t = dt * steps
+    assert abs(rec[-1, 0] - n0 * np.exp(-gamma * t)) <= n0 * (gamma * dt) ** 2 * gamma * t / 20
+
+
+def test_strang_trace_and_unitary_limit():
+    """Trace is kept exactly (tr L(X) = 0 in both stages); with no jumps the step is U rho U^+."""
+    m = W.hb_shaped(n_steps=100, record_every=50)
+    m.update(n_cavities=1, atoms_per_cavity=[2], n_max=[2], g=m["g"][:2], jumps=[(0, 0, 0.01), (2, 0, 0.02)])
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=7)
+    rho = oracle.evolve(m, rho0=rho0, basis=b, return_records=False, scheme="strang")
+    assert abs(np.trace(rho) - 1.0) < 1e-13
+    m0 = dict(m, jumps=[])
+    U = oracle.propagator(oracle.hamiltonian(m0, b), m0["dt"])
+    rho_u = oracle.evolve(m0, rho0=rho0, basis=b, return_records=False, scheme="strang")
+    Un = np.linalg.matrix_power(U, 100)
+    assert np.abs(rho_u - Un @ rho0 @ Un.conj().T).max() < 1e-12
