@@ -55,6 +55,14 @@ typedef enum {
     QED_SPLIT_TF32x3 = 3   /* reserved                                                    */
 } qed_precision;
 
+/* Time-stepping schemes for the two stages of Table 3 (the unitary evolution of Eq. 2 and
+ * the Lindblad term of Eq. 3; the paper does not state how they are combined). */
+enum {
+    QED_SCHEME_LIE = 0,    /* rho <- E(dt) U rho U^+, E(t) one explicit Euler step: first order */
+    QED_SCHEME_STRANG = 1  /* rho <- E2(dt/2) U E2(dt/2)(rho) U^+, E2(t) X = X + t L(X + t/2 L(X))
+                              (explicit midpoint rule): second order in dt                   */
+};
+
 /* Basis kinds (Sec. 4.2, Eqs. 10-11 restrict the 2^Area product space to one photon). */
 enum {
     QED_BASIS_FULL = 0,        /* full product space, mixed-radix order (first digit slowest) */
@@ -151,6 +159,13 @@ qed_status qed_n_observables(const qed_model *m, int32_t *n);
  * (0 = never; default 100).  Ignored in FP64. */
 qed_status qed_set_renorm_every(qed_model *m, int32_t every);
 
+/* The time-stepping scheme (QED_SCHEME_LIE, the default, or QED_SCHEME_STRANG) that
+ * qed_evolve and qed_evolve_batched use from now on; the Strang scheme runs four Lindblad
+ * stages per step instead of one.  EINVAL for an unknown scheme; ENOMEM if the FP64 path's
+ * stage buffer cannot be allocated.  Synchronises the device.  qed_adjoint differentiates
+ * the Lie step only (EUNSUPPORTED otherwise). */
+qed_status qed_set_scheme(qed_model *m, int32_t scheme);
+
 /* ---------------------------------------------------------------- hot path */
 
 /*
@@ -170,16 +185,22 @@ qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_off
 /*
  * Gradients of the loss L = tr(diag(obs_diag) rho_N) after n_steps steps from rho0 (device
  * complex128 D x D, not modified), by the discrete adjoint of the step qed_evolve takes
- * (Eq. 2 and Eq. 3, unitary part then one Euler step of the Lindblad term):
+ * with the Lie scheme (Eq. 2 and Eq. 3, unitary part then one Euler step of the Lindblad
+ * term):
  *   lambda_N = diag(obs_diag);  kappa = J^+(lambda_{n+1});  lambda_n = U^+ kappa U;
  *   dL/dgamma_j = dt sum_n tr(lambda_{n+1} D_j(V_n));
  *   dL/dtheta   = 2 dt Im tr(G dH/dtheta),  G = L_exp(-i dt H, sum_n rho_n U^+ kappa_{n+1}),
- * the Frechet derivative taken once as a block of exp([[X, M], [0, X]]).  rho is
- * checkpointed every `checkpoint_every` steps and recomputed in between.  Outputs are
+ * the Frechet derivative taken once (the Pade-13 approximant and its derivative, i.e. the
+ * upper-right block of exp([[X, M], [0, X]]) evaluated on D x D blocks).  rho is
+ * checkpointed every `checkpoint_every` steps; every segment but the last is recomputed
+ * during the backward pass (the forward pass stores the last one, so checkpoint_every >=
+ * n_steps recomputes nothing at the cost of 2 n_steps D^2 x 16 bytes).  Outputs are
  * device FP64: *loss; grad_g[total atoms], grad_zeta[n_bonds], grad_gamma[n_jumps] in the
- * order of the spec (each may be NULL only if its count is 0).  The FP64 kernels carry
- * the adjoint for every model precision.  Allocates its work space (checkpoints, one
- * segment of rho_n and V_n, the 2D x 2D block) per call; synchronises `stream`.
+ * order of the spec (each may be NULL only if its count is 0).  FP64 models use FP64
+ * kernels throughout; split-precision models run the forward steps, the co-state steps
+ * (as a backward model with U^+ and the outgoing jump lists) and the products
+ * rho_n lambda_n in split precision, accumulating M in FP64.  EUNSUPPORTED under
+ * QED_SCHEME_STRANG.  Allocates its work space per call; synchronises `stream`.
  */
 qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t checkpoint_every,
                        const double *obs_diag, double *loss, double *grad_g, double *grad_zeta,

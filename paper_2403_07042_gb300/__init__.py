@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libqed.so")
 QED_OK, QED_EINVAL, QED_ENOMEM, QED_ECUDA, QED_ETIMEOUT, QED_ENUMERIC, QED_EUNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "ENUMERIC", "EUNSUPPORTED"]
 PRECISIONS = {"fp64": 0, "split_fp16x2": 1, "split_bf16x3": 2, "split_tf32x3": 3}
+SCHEMES = {"lie": 0, "strang": 1}
 
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -75,6 +76,7 @@ def lib():
         "qed_basis_index": [vp, _c_int32_p, ctypes.POINTER(i64)],
         "qed_n_observables": [vp, _c_int32_p],
         "qed_set_renorm_every": [vp, i32],
+        "qed_set_scheme": [vp, i32],
         "qed_evolve": [vp, vp, i64, i64, i32, i32, _c_int32_p, vp, vp],
         "qed_observables": [vp, vp, i32, _c_int32_p, vp, vp],
         "qed_sync_status": [vp, vp],
@@ -233,7 +235,7 @@ def _stream_handle(stream):
 class Model:
     """A model built on the GPU: U = exp(-i H dt) and the operators, owned by libqed."""
 
-    def __init__(self, model, precision="fp64", dt=None, stream=None):
+    def __init__(self, model, precision="fp64", dt=None, stream=None, scheme="lie"):
         self.spec_dict = model
         self.precision = precision
         self.dt = float(model["dt"] if dt is None else dt)
@@ -249,6 +251,9 @@ class Model:
         _check(lib().qed_n_observables(self._h, ctypes.byref(n)), "qed_n_observables")
         self.n_observables = n.value
         self.n_digits = spec_dim(model)[1]
+        self.scheme = "lie"
+        if scheme != "lie":
+            self.set_scheme(scheme)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -288,6 +293,12 @@ class Model:
 
     def set_renorm_every(self, every):
         _check(lib().qed_set_renorm_every(self._h, int(every)), "qed_set_renorm_every")
+
+    def set_scheme(self, scheme):
+        """'lie' (first order) or 'strang' (second order: half Lindblad steps by the explicit
+        midpoint rule around the unitary)."""
+        _check(lib().qed_set_scheme(self._h, SCHEMES[scheme]), "qed_set_scheme")
+        self.scheme = scheme
 
     @staticmethod
     def n_records(n_steps, record_every, step_offset=0):

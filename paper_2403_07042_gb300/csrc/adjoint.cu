@@ -625,6 +625,10 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: n_steps >= 0 and checkpoint_every > 0 required");
         return QED_EINVAL;
     }
+    if (m->scheme != QED_SCHEME_LIE) {
+        set_error("qed_adjoint: only the Lie step is differentiated");
+        return QED_EUNSUPPORTED;
+    }
     ADJ_TRY(setup(m));
     AdjointState &a = *m->adj;
     if ((a.n_g > 0 && !grad_g) || (a.n_zeta > 0 && !grad_zeta) || (a.n_jumps > 0 && !grad_gamma)) {

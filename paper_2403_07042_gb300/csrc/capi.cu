@@ -48,8 +48,9 @@ void release(qed_model *m) {
     for (auto &g : m->graph)
         if (g) cudaGraphExecDestroy(g);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
-    void *ptrs[] = {m->U,      m->work1,  m->work2, m->phase,       m->anti,    m->in_ptr, m->in_jump,
-                    m->in_src, m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err,    m->rho_int};
+    void *ptrs[] = {m->U,      m->work1,   m->work2, m->work3,       m->phase,   m->anti, m->in_ptr,
+                    m->in_jump, m->in_src, m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err,
+                    m->rho_int};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->err_host) cudaFreeHost(m->err_host);
@@ -142,12 +143,45 @@ qed_status ensure_ids(qed_model *m, int32_t n_obs, const int32_t *ids, cudaStrea
 }
 
 
-// One FP64 step: V = (U rho) U^+, then the Lindblad update (Eq. 3) into rho.
-void step_f64(qed_model *m, double2 *rho, cudaStream_t s) {
+// One FP64 step.  Lie: V = (U rho) U^+, then the Euler update of Eq. 3 into rho.  Strang:
+// rho <- E(dt/2) rho, V = U rho U^+, rho <- E(dt/2) V, each E(t) X = X + t L(X + t/2 L(X))
+// as two stages through work3.  With `ev`, records an event before every kernel and after
+// the last; returns the number of kernels and names them in `label`.
+int step_f64(qed_model *m, double2 *rho, cudaStream_t s, cudaEvent_t *ev = nullptr, std::string *label = nullptr) {
     const int64_t D = m->D;
+    const double dt = m->dt;
+    const bool strang = m->scheme == QED_SCHEME_STRANG;
+    int e = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[e], s);
+        ++e;
+    };
+    auto stage = [&](const double2 *X, const double2 *B, double2 *out, double tau) {
+        lindblad_axpy_f64(s, D, X, B, out, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, tau);
+    };
+    if (strang) {
+        mark();
+        stage(rho, rho, m->work3, 0.25 * dt);
+        mark();
+        stage(m->work3, rho, rho, 0.5 * dt);
+    }
+    mark();
     zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);
+    mark();
     zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
-    dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, m->dt);
+    mark();
+    if (strang) {
+        stage(m->work2, m->work2, m->work3, 0.25 * dt);
+        mark();
+        stage(m->work3, m->work2, rho, 0.5 * dt);
+    } else {
+        dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, dt);
+    }
+    mark();
+    if (label)
+        *label = strang ? "lindblad_a,lindblad_b,zgemm_f64_1,zgemm_f64_2,lindblad_c,lindblad_d"
+                        : "zgemm_f64_1,zgemm_f64_2,dissipate_f64";
+    return e - 1;
 }
 
 void one_step(qed_model *m, cudaStream_t s) {
@@ -377,6 +411,23 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every) {
     return QED_OK;
 }
 
+qed_status qed_set_scheme(qed_model *m, int32_t scheme) {
+    if (!m || (scheme != QED_SCHEME_LIE && scheme != QED_SCHEME_STRANG)) return einval("bad scheme");
+    if (scheme == m->scheme) return QED_OK;
+    if (scheme == QED_SCHEME_STRANG && m->prec == QED_FP64 && !m->work3)
+        QED_TRY(dev_alloc(&m->work3, (size_t)(m->D * m->D)));
+    // the captured step graphs belong to the old scheme
+    QED_CUDA_TRY(cudaDeviceSynchronize());
+    for (auto &g : m->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    m->scheme = scheme;
+    split_set_scheme(m, scheme);
+    return QED_OK;
+}
+
 qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_offset, int32_t record_every,
                       int32_t n_obs, const int32_t *obs_ids, double *records, qed_stream stream) {
     if (!m || !rho_v) return einval("NULL model or rho");
@@ -571,16 +622,7 @@ qed_status qed_profile(qed_model *m, void *rho_v, int64_t n_steps, double *ms, i
     if (m->prec != QED_FP64) QED_TRY(split_begin(m, rho, s));
     for (int64_t i = 0; i < n_steps; ++i) {
         if (m->prec == QED_FP64) {
-            const int64_t D = m->D;
-            cudaEventRecord(m->ev[0], s);
-            zgemm(s, D, D, D, 1.0, m->U, D, rho, D, false, 0.0, m->work1, D);
-            cudaEventRecord(m->ev[1], s);
-            zgemm(s, D, D, D, 1.0, m->work1, D, m->U, D, true, 0.0, m->work2, D);
-            cudaEventRecord(m->ev[2], s);
-            dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, m->dt);
-            cudaEventRecord(m->ev[3], s);
-            classes = 3;
-            label = "zgemm_f64_1,zgemm_f64_2,dissipate_f64";
+            classes = step_f64(m, rho, s, m->ev, &label);
         } else {
             classes = split_step_timed(m, s, label);
         }

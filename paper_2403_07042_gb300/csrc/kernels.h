@@ -55,6 +55,12 @@ void dissipate_f64(cudaStream_t s, int64_t D, const double2 *V, double2 *rho, co
                    const int32_t *in_ptr, const int32_t *in_jump, const int32_t *in_src,
                    const double *in_coef, double dt);
 
+// out = B + tau [ -(d_m + d_n)/2 X_mn + sum_j c_j(m) c_j(n) X[src_j(m), src_j(n)] ] (out may be
+// B, not X): a stage of the explicit midpoint rule for the Lindblad term.
+void lindblad_axpy_f64(cudaStream_t s, int64_t D, const double2 *X, const double2 *B, double2 *out,
+                       const double *anti, const int32_t *in_ptr, const int32_t *in_jump, const int32_t *in_src,
+                       const double *in_coef, double tau);
+
 // out[o] = rho_kk (id < D), or sum_k w[id-D][k] rho_kk; deterministic block reduction.
 void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights,
                  const int32_t *ids, int32_t n_obs, double *out);

@@ -262,6 +262,40 @@ __global__ void take_right_half_kernel(int64_t D, const double2 *aug, double2 *R
     R[idx] = aug[(idx / D) * 2 * D + D + idx % D];
 }
 
+// out = B + tau [ -(d_m + d_n)/2 X_mn + sum_j c_j(m) c_j(n) X[src_j(m), src_j(n)] ]: a stage
+// of the explicit midpoint rule for the Lindblad term (Eq. 3).  out may be B (each
+// element reads only its own B entry), never X.
+__global__ void lindblad_axpy_f64_kernel(int64_t D, const double2 *__restrict__ X, const double2 *B, double2 *out,
+                                         const double *__restrict__ anti, const int32_t *__restrict__ in_ptr,
+                                         const int32_t *__restrict__ in_jump, const int32_t *__restrict__ in_src,
+                                         const double *__restrict__ in_coef, double tau) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (m >= D || n >= D) return;
+    const double2 x = X[m * D + n];
+    const double h = -0.5 * (anti[m] + anti[n]);
+    double2 l = make_double2(h * x.x, h * x.y);
+    int a = in_ptr[m], ae = in_ptr[m + 1];
+    int b = in_ptr[n], be = in_ptr[n + 1];
+    while (a < ae && b < be) {  // jumps present in both incoming lists
+        const int ja = in_jump[a], jb = in_jump[b];
+        if (ja < jb) {
+            ++a;
+        } else if (ja > jb) {
+            ++b;
+        } else {
+            const double c = in_coef[a] * in_coef[b];
+            const double2 g = X[(int64_t)in_src[a] * D + in_src[b]];
+            l.x = fma(c, g.x, l.x);
+            l.y = fma(c, g.y, l.y);
+            ++a;
+            ++b;
+        }
+    }
+    const double2 base = B[m * D + n];
+    out[m * D + n] = make_double2(fma(tau, l.x, base.x), fma(tau, l.y, base.y));
+}
+
 __global__ void dissipate_f64_kernel(int64_t D, const double2 *__restrict__ V, double2 *__restrict__ rho,
                                      const double *__restrict__ anti, const int32_t *__restrict__ in_ptr,
                                      const int32_t *__restrict__ in_jump, const int32_t *__restrict__ in_src,
@@ -441,6 +475,15 @@ void dissipate_f64(cudaStream_t s, int64_t D, const double2 *V, double2 *rho, co
     dim3 block(32, 8);
     dim3 grid(blocks_for(D, 32), blocks_for(D, 8));
     dissipate_f64_kernel<<<grid, block, 0, s>>>(D, V, rho, anti, in_ptr, in_jump, in_src, in_coef, dt);
+}
+
+void lindblad_axpy_f64(cudaStream_t s, int64_t D, const double2 *X, const double2 *B, double2 *out,
+                       const double *anti, const int32_t *in_ptr, const int32_t *in_jump, const int32_t *in_src,
+                       const double *in_coef, double tau) {
+    count_launches(1);
+    dim3 block(32, 8);
+    dim3 grid(blocks_for(D, 32), blocks_for(D, 8));
+    lindblad_axpy_f64_kernel<<<grid, block, 0, s>>>(D, X, B, out, anti, in_ptr, in_jump, in_src, in_coef, tau);
 }
 
 void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights, const int32_t *ids,

@@ -46,11 +46,13 @@ struct qed_model {
     double dt = 0.0;
     qed_precision prec = QED_FP64;
     int32_t renorm_every = 100;
+    int32_t scheme = QED_SCHEME_LIE;
 
     // device operators (FP64, complex interleaved)
     double2 *U = nullptr;        // D x D
     double2 *work1 = nullptr;    // D x D
     double2 *work2 = nullptr;    // D x D
+    double2 *work3 = nullptr;    // D x D stage buffer of the Strang step (FP64 path, on demand)
     double2 *phase = nullptr;    // D: P_k = exp(-i H_kk dt)
     double *anti = nullptr;      // D: d_k = sum_j gamma_j (A_j^+A_j)_kk
     // incoming jump lists per row m, sorted by jump id: entries [in_ptr[m], in_ptr[m+1])

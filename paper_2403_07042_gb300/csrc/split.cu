@@ -43,7 +43,7 @@ struct InstDesc {
     float s_rho;            // scale of the rho planes
     float *part;            // split-K partial sums (GEMM1, then GEMM2)
     float *w32, *wt32;
-    float4 *rho, *V;
+    float4 *rho, *V, *Y;    // state, V = U rho U^+, stage buffer of the Strang step
     const float4 *phase;
     const float2 *damp;
     const int32_t *in_ptr, *in_jump, *in_src;
@@ -76,6 +76,7 @@ struct Batch {
     int n_wtiles = 0, n_etiles = 0;
     int cs1 = 1, cs2 = 1;  // split-K slices of GEMM1 / GEMM2
     bool w_reduce = false;  // GEMM1 split: a separate pass sums its slices into W
+    int scheme = QED_SCHEME_LIE;
     int bn1 = 256, bn2 = 256;  // tile widths (one per grouped launch)
     void release() {
         void *ptrs[] = {desc, jobs1, jobs2, maps, items1, items2, wtiles, etiles};
@@ -100,6 +101,7 @@ struct SplitState {
     float *wt32 = nullptr;    // [2][Dp][Dp]  W^T (re plane, im plane)
     float *partial = nullptr; // split-K slices of either product; GEMM2's sum X at slice 0
     float4 *rho_df[2] = {nullptr, nullptr};  // D x D {re_hi, re_lo, im_hi, im_lo}: rho, then V
+    float4 *y_df = nullptr;                  // D x D stage buffer of the Strang step
     float4 *phase_df = nullptr;              // D: P_k as {re_hi, re_lo, im_hi, im_lo}
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
     float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
@@ -349,11 +351,21 @@ __global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict_
     a.V[m * a.D + n] = store_cdf(cdf_mul(cdf_mul_conj(pm, pn), r));
 }
 
-// Eq. (3) on V: rho_mn = V_mn - (dt/2)(d_m + d_n) V_mn + dt sum_j c_j(m) c_j(n) V[src_j(m), src_j(n)];
-// the two correction terms (relative size dt gamma) are formed to FP32 accuracy and added
-// to the double-float V.  Also writes the FP16 planes of rho for the next GEMM1.
-__global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
-                                                           const InstDesc *__restrict__ descs) {
+// The Lindblad term of Eq. (3) as an update of the double-float buffers:
+//   out_mn = B_mn + f [ -(dt/2)(d_m + d_n) X_mn + dt sum_j c_j(m) c_j(n) X[src_j(m), src_j(n)] ],
+// f a power of two (exact).  The correction (relative size dt gamma) is formed to FP32
+// accuracy and added to the double-float B.  With X = B = V, f = 1 and out = rho this is
+// the Euler step of the Lie splitting; with f = 1/4 and 1/2 it gives the two stages of the
+// explicit midpoint rule of the Strang splitting.  Optionally writes the FP16 planes of out
+// (the next GEMM1's operand).  Buffers are chosen by index: 0 rho, 1 V, 2 the stage buffer.
+__device__ __forceinline__ float4 *state_buf(const InstDesc &a, int sel) {
+    return sel == 0 ? a.rho : (sel == 1 ? a.V : a.Y);
+}
+
+template <bool LIE>
+__device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ tiles,
+                                                const InstDesc *__restrict__ descs, int xsel, int bsel, int osel,
+                                                float f, bool planes) {
     // set-up tables (damping, padded jump rows) are read while the previous kernel finishes
     const TileItem it = tiles[blockIdx.x];
     const InstDesc a = descs[it.inst];
@@ -371,10 +383,13 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__res
             en[i] = a.in_tab[nc * kInMax + i];
         }
     }
+    const float4 *X = LIE ? a.V : state_buf(a, xsel);
+    const float4 *B = LIE ? a.V : state_buf(a, bsel);
+    float4 *O = LIE ? a.rho : state_buf(a, osel);
     pdl_wait();
     pdl_trigger();
     if (!inside) return;
-    const cdf v = load_cdf(a.V[m * D + n]);
+    const cdf v = load_cdf(X[m * D + n]);
     const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
     float gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
     float gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
@@ -397,7 +412,7 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__res
                 }
             hit[i] = h && em[i].x != kNoJump;
             cq[i] = c2;
-            u[i] = hit[i] ? a.V[(int64_t)em[i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
+            u[i] = hit[i] ? X[(int64_t)em[i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < kInMax; ++i) {
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__res
         } else {
             const float2 cp = a.coef[p], cq = a.coef[q];
             const df c = df_mul({cp.x, cp.y}, {cq.x, cq.y});  // dt c_j(m) c_j(n)
-            const float4 u = a.V[(int64_t)a.in_src[p] * D + a.in_src[q]];
+            const float4 u = X[(int64_t)a.in_src[p] * D + a.in_src[q]];
             const float ur = u.x + u.y, ui = u.z + u.w;
             gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
             gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
@@ -427,10 +442,12 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__res
             ++q;
         }
     }
+    const cdf b = LIE ? v : load_cdf(B[m * D + n]);
     cdf out;
-    out.re = df_add_f(v.re, gr);
-    out.im = df_add_f(v.im, gi);
-    a.rho[m * D + n] = store_cdf(out);
+    out.re = df_add_f(b.re, LIE ? gr : f * gr);
+    out.im = df_add_f(b.im, LIE ? gi : f * gi);
+    O[m * D + n] = store_cdf(out);
+    if (!LIE && !planes) return;
     const int64_t plane = a.Dp * 2 * a.Dp;
     __half h, l;
     df_to_half2(out.re, a.s_rho, h, l);
@@ -439,6 +456,19 @@ __global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__res
     df_to_half2(out.im, a.s_rho, h, l);
     a.rho_pl[m * 2 * a.Dp + a.Dp + n] = h;
     a.rho_pl[plane + m * 2 * a.Dp + a.Dp + n] = l;
+}
+
+// Lie step: rho = V + dt L(V), and the next planes.
+__global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
+                                                           const InstDesc *__restrict__ descs) {
+    lindblad_update<true>(tiles, descs, 1, 1, 0, 1.f, true);
+}
+
+// One stage of the Strang step: out = B + f dt L(X).
+__global__ void __launch_bounds__(256) lindblad_df_kernel(const TileItem *__restrict__ tiles,
+                                                          const InstDesc *__restrict__ descs, int xsel, int bsel,
+                                                          int osel, float f, int planes) {
+    lindblad_update<false>(tiles, descs, xsel, bsel, osel, f, planes != 0);
 }
 
 __global__ void __launch_bounds__(256) observables_df_kernel(int64_t D, const float4 *st, const double *w,
@@ -559,6 +589,12 @@ qed_status upload(T **dst, const std::vector<T> &v) {
 qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
     b.release();
     b.n = n;
+    b.scheme = ms[0]->scheme;
+    for (int i = 1; i < n; ++i)
+        if (ms[i]->scheme != b.scheme) {
+            set_error("batched evolution: all models must use one time-stepping scheme");
+            return QED_EINVAL;
+        }
     std::vector<InstDesc> desc((size_t)n);
     std::vector<GemmJob> jobs1((size_t)n), jobs2((size_t)n);
     std::vector<CUtensorMap> maps((size_t)(4 * n));
@@ -585,6 +621,7 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.wt32 = S.wt32;
         d.rho = S.rho_df[0];
         d.V = S.rho_df[1];
+        d.Y = S.y_df;
         d.phase = S.phase_df;
         d.damp = S.damp_df;
         d.in_ptr = m->in_ptr;
@@ -696,6 +733,17 @@ void launch_dissipate(const Batch &b, cudaStream_t s) {
     launch_pdl(dissipate_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
     count_launches(1);
 }
+void launch_lindblad(const Batch &b, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s) {
+    launch_pdl(lindblad_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc, xsel, bsel, osel, f,
+               planes);
+    count_launches(1);
+}
+// The two stages of one explicit-midpoint half step of the Lindblad flow (step dt/2):
+// Y = X + (dt/4) L(X), then rho = X + (dt/2) L(Y) with its planes.
+void launch_half_lindblad(const Batch &b, int xsel, cudaStream_t s) {
+    launch_lindblad(b, xsel, xsel, 2, 0.25f, 0, s);
+    launch_lindblad(b, 2, xsel, 0, 0.5f, 1, s);
+}
 
 }  // namespace
 
@@ -719,6 +767,7 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         SPLIT_TRY(alloc(&S.wt32, (size_t)2 * Dp * Dp));
         SPLIT_TRY(alloc(&S.rho_df[0], (size_t)(D * D)));
         SPLIT_TRY(alloc(&S.rho_df[1], (size_t)(D * D)));
+        SPLIT_TRY(alloc(&S.y_df, (size_t)(D * D)));
         SPLIT_TRY(alloc(&S.phase_df, (size_t)D));
         QED_CUDA_TRY(cudaMemset(S.rho_pl, 0, pl * sizeof(__half)));
         QED_CUDA_TRY(cudaMemset(S.w_pl, 0, pl * sizeof(__half)));
@@ -820,17 +869,47 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
 }
 
 void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
+    if (b.scheme == QED_SCHEME_STRANG) launch_half_lindblad(b, 0, s);  // rho <- E(dt/2) rho
     launch_gemm1(b, err, s);  // unsplit: its epilogue writes W, W^T and the W planes
     if (b.w_reduce) launch_w_reduce(b, s);
     launch_gemm2(b, err, s);
     launch_form(b, s);
-    launch_dissipate(b, s);
+    if (b.scheme == QED_SCHEME_STRANG)
+        launch_half_lindblad(b, 1, s);  // rho <- E(dt/2) V
+    else
+        launch_dissipate(b, s);
 }
 
 void split_step(qed_model *m, cudaStream_t s) { batch_step(m->sp->self, m->err, s); }
 
+void split_set_scheme(qed_model *m, int scheme) {
+    if (m->sp) m->sp->self.scheme = scheme;
+}
+
 int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
     const Batch &b = m->sp->self;
+    if (b.scheme == QED_SCHEME_STRANG) {
+        int e = 0;
+        cudaEventRecord(m->ev[e++], s);
+        launch_lindblad(b, 0, 0, 2, 0.25f, 0, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_lindblad(b, 2, 0, 0, 0.5f, 1, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_gemm1(b, m->err, s);
+        cudaEventRecord(m->ev[e++], s);
+        if (b.w_reduce) launch_w_reduce(b, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_gemm2(b, m->err, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_form(b, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_lindblad(b, 1, 1, 2, 0.25f, 0, s);
+        cudaEventRecord(m->ev[e++], s);
+        launch_lindblad(b, 2, 1, 0, 0.5f, 1, s);
+        cudaEventRecord(m->ev[e++], s);
+        label = "lindblad_a,lindblad_b,gemm1_tc,w_reduce,gemm2_tc,form_v,lindblad_c,lindblad_d";
+        return 8;
+    }
     cudaEventRecord(m->ev[0], s);
     launch_gemm1(b, m->err, s);
     cudaEventRecord(m->ev[1], s);
@@ -914,7 +993,8 @@ void split_release(qed_model *m) {
     SplitState &S = *m->sp;
     S.self.release();
     void *ptrs[] = {S.a1,        S.b2,        S.rho_pl,   S.w_pl,    S.w32,     S.wt32,
-                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df, S.in_tab};
+                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df, S.in_tab,
+                    S.y_df};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m->sp;
