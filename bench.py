@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="split_fp16x2")
+    p.add_argument("--scheme", default="lie", choices=["lie", "strang"],
+                   help="time-stepping scheme (the adjoint workload differentiates the Lie step only)")
     p.add_argument("--qme-steps", type=int, default=None)
     p.add_argument("--fp64-qme-steps", type=int, default=200)
     p.add_argument("--cpu-sample", type=int, default=40, help="oracle QME steps in the CPU baseline")
@@ -190,7 +192,7 @@ def run_ours(args):
     model = W.hb_shaped()
     qme_steps = args.qme_steps or model["n_steps"]
     r = model["record_every"]
-    gm = qed.Model(model, precision=args.precision)
+    gm = qed.Model(model, precision=args.precision, scheme=args.scheme)
     D = gm.dim
     obs = list(range(D))
     i0 = gm.initial_index()
@@ -238,7 +240,7 @@ def run_ours(args):
     value = world * args.steps * qme_steps / (t_max / 1e3)
 
     # parity of this run's final state against the stored oracle trajectory, if present
-    parity = parity_against_golden(rho, records, qme_steps)
+    parity = parity_against_golden(rho, records, qme_steps) if args.scheme == "lie" else None
 
     # end to end: pinned host rho0 -> device, evolve, records + final rho -> host
     h_rho0 = rho0.cpu().pin_memory()
@@ -272,7 +274,7 @@ def run_ours(args):
     # the all-FP64 GPU path on the same workload (shorter run)
     fp64 = None
     if args.precision != "fp64" and args.fp64_qme_steps > 0:
-        g64 = qed.Model(model, precision="fp64")
+        g64 = qed.Model(model, precision="fp64", scheme=args.scheme)
         rho64 = rho0.clone()
         g64.evolve(rho64, 5)
         torch.cuda.synchronize(dev)
@@ -303,7 +305,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f16x2->f32 (split), f64 master" if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "dim": D, "qme_steps_per_step": qme_steps, "dt": model["dt"],
-                   "record_every": r, "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "record_every": r, "precision": args.precision, "scheme": args.scheme,
+                   "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) between timed iterations; working set < L2 within a run"},
         "complex_tflops": complex_tflops(D, value / world) * world,
         "parity_vs_oracle": parity,
@@ -391,7 +394,7 @@ def run_other(args):
     if wl == "batched_chains":
         specs = W.batched_chains(args.instances, seed=0)
         steps = args.qme_steps or specs[0]["n_steps"]
-        models = [qed.Model(m, precision=prec) for m in specs]
+        models = [qed.Model(m, precision=prec, scheme=args.scheme) for m in specs]
         dims = [gm.dim for gm in models]
         rho0 = []
         for gm in models:
@@ -414,7 +417,7 @@ def run_other(args):
         m = {"jch2_d36": W.jch_two_cavities, "lattice_32x32_d2049": W.lattice,
              "adjoint_lattice_24x24_d1153": W.adjoint_lattice}[wl]()
         steps = args.qme_steps or m["n_steps"]
-        gm = qed.Model(m, precision=prec)
+        gm = qed.Model(m, precision=prec, scheme=args.scheme)
         D = gm.dim
         rho0 = torch.zeros((D, D), dtype=torch.complex128, device=dev)
         i0 = gm.initial_index()
@@ -465,7 +468,7 @@ def run_other(args):
         "metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16x2->f32 (split), f64 master" if prec != "fp64" else "f64", "data": "synthetic",
-        "config": dict({"workload": wl, "qme_steps_per_step": steps, "precision": prec,
+        "config": dict({"workload": wl, "qme_steps_per_step": steps, "precision": prec, "scheme": args.scheme,
                         "l2": "flushed (512 MB write) between timed iterations"}, **extra),
         "complex_tflops": flops * qme_rate / 1e12, "gpu_launches": launches, "clocks": clocks,
     }
