@@ -375,13 +375,12 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     const bool inside = m < D && n < D;
     const int64_t mc = inside ? m : 0, nc = inside ? n : 0;
     const float2 dm = a.damp[mc], dn = a.damp[nc];
+    // the row's padded jump entries are the same for the whole warp (one m per warp): read
+    // them before the wait; the column's entries after it, to keep the register count low
     int4 em[kInMax], en[kInMax];
     if (a.in_tab) {
 #pragma unroll
-        for (int i = 0; i < kInMax; ++i) {
-            em[i] = a.in_tab[mc * kInMax + i];
-            en[i] = a.in_tab[nc * kInMax + i];
-        }
+        for (int i = 0; i < kInMax; ++i) em[i] = a.in_tab[mc * kInMax + i];
     }
     const float4 *X = LIE ? a.V : state_buf(a, xsel);
     const float4 *B = LIE ? a.V : state_buf(a, bsel);
@@ -390,6 +389,10 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     pdl_trigger();
     if (!inside) return;
     const cdf v = load_cdf(X[m * D + n]);
+    if (a.in_tab) {
+#pragma unroll
+        for (int i = 0; i < kInMax; ++i) en[i] = a.in_tab[nc * kInMax + i];
+    }
     const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
     float gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
     float gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
@@ -459,13 +462,13 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
 }
 
 // Lie step: rho = V + dt L(V), and the next planes.
-__global__ void __launch_bounds__(256) dissipate_df_kernel(const TileItem *__restrict__ tiles,
+__global__ void __launch_bounds__(256, 4) dissipate_df_kernel(const TileItem *__restrict__ tiles,
                                                            const InstDesc *__restrict__ descs) {
     lindblad_update<true>(tiles, descs, 1, 1, 0, 1.f, true);
 }
 
 // One stage of the Strang step: out = B + f dt L(X).
-__global__ void __launch_bounds__(256) lindblad_df_kernel(const TileItem *__restrict__ tiles,
+__global__ void __launch_bounds__(256, 4) lindblad_df_kernel(const TileItem *__restrict__ tiles,
                                                           const InstDesc *__restrict__ descs, int xsel, int bsel,
                                                           int osel, float f, int planes) {
     lindblad_update<false>(tiles, descs, xsel, bsel, osel, f, planes != 0);
