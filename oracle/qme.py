@@ -437,7 +437,48 @@ def evolve(model, rho0=None, n_steps=None, record_every=None, obs_ids=None, U=No
     return rho
 
 
-# ------------------------------------------------------------------ brute force
+# ------------------------------------------------------------------ state selection
+def select_states(model, eps, steps_per_round, n_rounds, rho0=None, basis=None, scheme="lie"):
+    """The state space selection of Sec. 3.2: rounds of {solve the QME for T =
+    steps_per_round * dt; growth speed of each state's probability,
+    |p_k(t + T) - p_k(t)| / T; delete every state whose growth speed is below eps;
+    normalise the density matrix of the remaining states}.  H and the A_j of the remaining
+    states are the projections P H P and P A_j P onto them.
+
+    Reading: taken literally a populated state whose probability happens to stay constant
+    would be deleted; a state whose probability is at least eps is kept.
+
+    Returns (kept indices into the original basis, final rho on them, sizes after each
+    round)."""
+    basis = basis or enumerate_basis(model)
+    dt = model["dt"]
+    H = hamiltonian(model, basis)
+    jumps = jump_operators(model, basis)
+    advance = STEPS[scheme]
+    keep = np.arange(basis.dim)
+    rho = initial_density(model, basis) if rho0 is None else np.array(rho0, dtype=np.complex128)
+    T = steps_per_round * dt
+    sizes = []
+    for _ in range(n_rounds):
+        Hs = H[np.ix_(keep, keep)]
+        Us = propagator(Hs, dt)
+        js = [(g, sp.csr_matrix(A[keep][:, keep])) for g, A in jumps]
+        p0 = np.real(np.diag(rho)).copy()
+        for _ in range(steps_per_round):
+            rho = advance(rho, Us, js, dt)
+        p1 = np.real(np.diag(rho))
+        growth = np.abs(p1 - p0) / T
+        local = np.flatnonzero((growth >= eps) | (p1 >= eps))
+        if len(local) == 0:
+            raise ValueError("every state fell below eps")
+        rho = rho[np.ix_(local, local)]
+        rho = 0.5 * (rho + rho.conj().T) / np.trace(rho).real
+        keep = keep[local]
+        sizes.append(len(keep))
+    return keep, rho, sizes
+
+
+# ------------------------------------------------------------------ brute force# ------------------------------------------------------------------ brute force
 def vec(X):
     """Column-stacking vectorisation."""
     return np.asarray(X).reshape(-1, order="F")

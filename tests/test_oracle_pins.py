@@ -474,3 +474,59 @@ def test_strang_trace_and_unitary_limit():
     rho_u = oracle.evolve(m0, rho0=rho0, basis=b, return_records=False, scheme="strang")
     Un = np.linalg.matrix_power(U, 100)
     assert np.abs(rho_u - Un @ rho0 @ Un.conj().T).max() < 1e-12
+
+
+# ---------------------------------------------------------------- state selection (Sec. 3.2)
+def test_selection_with_eps_zero_keeps_every_state_and_the_trajectory():
+    """eps = 0 deletes nothing: the rounds reproduce the plain trajectory (each round's
+    normalisation divides by a trace that is 1 to rounding)."""
+    m = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+             zeta=[0.006], dt=0.1)
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=3)
+    keep, rho, sizes = oracle.select_states(m, 0.0, 40, 3, rho0=rho0, basis=b)
+    assert sizes == [b.dim] * 3 and np.array_equal(keep, np.arange(b.dim))
+    ref = oracle.evolve(m, rho0=rho0, n_steps=120, basis=b, return_records=False)
+    assert np.abs(rho - ref).max() < 1e-13
+
+
+def _reachable(H, start):
+    """States connected to `start` through nonzero entries of H (breadth-first search)."""
+    seen, front = {start}, [start]
+    while front:
+        nxt = []
+        for k in front:
+            for j in np.flatnonzero(H[:, k]):
+                if j not in seen:
+                    seen.add(int(j))
+                    nxt.append(int(j))
+        front = nxt
+    return np.array(sorted(seen))
+
+
+def test_selection_keeps_exactly_the_reachable_states_of_a_closed_model():
+    """Without jumps the dynamics stays in the subspace H connects to the initial state;
+    every other state has probability exactly zero and is deleted at any eps > 0, and the
+    reduced trajectory equals the full one restricted to the kept states."""
+    m = W.jch_two_cavities(gamma=0.0)
+    m["jumps"] = []
+    b = oracle.enumerate_basis(m)
+    H = oracle.hamiltonian(m, b)
+    k0 = oracle.initial_index(m, b)
+    keep, rho, sizes = oracle.select_states(m, 1e-35, 50, 2, basis=b)
+    assert np.array_equal(keep, _reachable(H, k0))
+    assert len(keep) < b.dim
+    full = oracle.evolve(m, n_steps=100, basis=b, return_records=False)
+    assert np.abs(full[np.ix_(keep, keep)] - rho).max() < 1e-13
+    assert np.abs(np.delete(np.diag(full), keep)).max() == 0.0
+
+
+def test_selection_rounds_normalise_and_shrink():
+    m = W.hb_shaped()
+    b = oracle.enumerate_basis(m)
+    keep, rho, sizes = oracle.select_states(m, 1e-20, 100, 3, basis=b)
+    assert all(x >= y for x, y in zip(sizes, sizes[1:])) and sizes[-1] == len(keep) < b.dim
+    assert abs(np.trace(rho).real - 1.0) < 1e-14
+    assert np.abs(rho - rho.conj().T).max() < 1e-15
+    assert oracle.initial_index(m, b) in keep
