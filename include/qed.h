@@ -221,6 +221,28 @@ qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t 
 qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos, int64_t n_steps,
                               int32_t record_every, double *const *records, qed_stream stream);
 
+/*
+ * State space selection (Sec. 3.2, "State space selection algorithm"; Table 1): starting
+ * from rho0 (device complex128 D x D of model m, not modified), n_rounds rounds of
+ *   solve:      qed_evolve for steps_per_round steps with the current model;
+ *   growth:     g_k = |p_k(t + T) - p_k(t)| / T of each state's probability p_k = rho_kk,
+ *               T = steps_per_round * dt;
+ *   comparison: delete every state with g_k < eps (a state whose probability is at least
+ *               eps is kept: a stationary populated state is not what the paper deletes);
+ *   normalise:  rho <- the remaining states' block, (rho + rho^+) / (2 tr rho);
+ * the model of the remaining states is H and every A_j projected onto them (P H P,
+ * P A_j P), with m's dt, precision, scheme and renormalisation interval.  Outputs:
+ * *out_model, a new model on the kept states (caller frees it with qed_free; m is left as
+ * it was); rho_out (device complex128, capacity D x D) the final n x n density matrix;
+ * keep (host int64 [D]) the kept states' indices in m's basis, increasing, first *n_keep
+ * valid; sizes (host int64 [n_rounds], or NULL) the dimension after each round.
+ * EINVAL for bad arguments, ENUMERIC if every state falls below eps or a trace is not
+ * finite.  Allocates its work space; synchronises `stream`.
+ */
+qed_status qed_select_states(qed_model *m, const void *rho0, int64_t steps_per_round, int32_t n_rounds, double eps,
+                             qed_model **out_model, void *rho_out, int64_t *keep, int64_t *n_keep, int64_t *sizes,
+                             qed_stream stream);
+
 /* Observables of one rho (device) into out (device FP64 [n_obs]). */
 qed_status qed_observables(const qed_model *m, const void *rho, int32_t n_obs,
                            const int32_t *obs_ids, double *out, qed_stream stream);

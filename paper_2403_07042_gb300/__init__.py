@@ -86,6 +86,8 @@ def lib():
         "qed_launch_count": [ctypes.POINTER(i64)],
         "qed_adjoint": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "qed_evolve_batched": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, i32, ctypes.POINTER(vp), vp],
+        "qed_select_states": [vp, vp, i64, i32, dbl, ctypes.POINTER(vp), vp, ctypes.POINTER(i64),
+                              ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
         "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
         "qed_tc_gemm_static": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
     }
@@ -255,6 +257,24 @@ class Model:
         if scheme != "lie":
             self.set_scheme(scheme)
 
+    @classmethod
+    def _from_handle(cls, h, parent):
+        """Wraps a library-built model (e.g. one on a selected subset of parent's basis)."""
+        self = cls.__new__(cls)
+        self.spec_dict = parent.spec_dict
+        self.precision = parent.precision
+        self.dt = parent.dt
+        self._h = h
+        d = ctypes.c_int64()
+        _check(lib().qed_dim(self._h, ctypes.byref(d)), "qed_dim")
+        self.dim = d.value
+        n = ctypes.c_int32()
+        _check(lib().qed_n_observables(self._h, ctypes.byref(n)), "qed_n_observables")
+        self.n_observables = n.value
+        self.n_digits = parent.n_digits
+        self.scheme = parent.scheme
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             lib().qed_free(self._h)
@@ -396,6 +416,29 @@ def evolve_batched(models, rhos, n_steps, record_every=0, records=None, stream=N
     _check(lib().qed_evolve_batched(n, H, R, int(n_steps), int(record_every), rec, _stream_handle(stream)),
            "qed_evolve_batched")
     return records
+
+
+def select_states(model, rho0, steps_per_round, n_rounds, eps, stream=None):
+    """State space selection (qed_select_states): rounds of solving, deleting the states
+    whose probability grows slower than eps, and normalising.  Returns (Model on the kept
+    states, its density matrix as a CUDA complex128 tensor, kept indices in model's basis,
+    dimension after each round)."""
+    import torch
+    _check_rho(rho0, model.dim)
+    D = model.dim
+    out = torch.zeros(D * D, dtype=torch.complex128, device=rho0.device)
+    keep = np.zeros(D, dtype=np.int64)
+    sizes = np.zeros(n_rounds, dtype=np.int64)
+    n = ctypes.c_int64()
+    h = ctypes.c_void_p()
+    _check(lib().qed_select_states(model._h, ctypes.c_void_p(rho0.data_ptr()), int(steps_per_round), int(n_rounds),
+                                   float(eps), ctypes.byref(h), ctypes.c_void_p(out.data_ptr()),
+                                   keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(n),
+                                   sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream_handle(stream)),
+           "qed_select_states")
+    k = n.value
+    reduced = Model._from_handle(h, model)
+    return reduced, out[:k * k].view(k, k).clone(), keep[:k].copy(), sizes
 
 
 def _check_rho(rho, dim):

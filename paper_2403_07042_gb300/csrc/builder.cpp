@@ -342,6 +342,65 @@ qed_status build_host_model(const qed_spec *spec, HostModel &hm, std::string &er
     return QED_OK;
 }
 
+bool restrict_host_model(const HostModel &src, const std::vector<int64_t> &keep, HostModel &dst,
+                         std::string &err) {
+    const int n = src.layout.n_digits();
+    std::vector<int64_t> to_new((size_t)src.dim, -1);
+    for (size_t a = 0; a < keep.size(); ++a) {
+        const int64_t k = keep[a];
+        if (k < 0 || k >= src.dim || (a > 0 && k <= keep[a - 1])) {
+            err = "kept indices must be increasing and inside the basis";
+            return false;
+        }
+        to_new[(size_t)k] = (int64_t)a;
+    }
+    if (keep.empty()) {
+        err = "no state kept";
+        return false;
+    }
+    dst = HostModel();
+    // the specification, its layout and the parameter tables are unchanged
+    dst.n_cavities = src.n_cavities;
+    dst.n_extra = src.n_extra;
+    dst.basis_kind = src.basis_kind;
+    dst.excitation_cap = src.excitation_cap;
+    dst.dim_cap = src.dim_cap;
+    dst.omega_c = src.omega_c;
+    dst.omega_a = src.omega_a;
+    dst.atoms_per_cavity = src.atoms_per_cavity;
+    dst.n_max = src.n_max;
+    dst.g = src.g;
+    dst.zeta = src.zeta;
+    dst.extra_tunnel = src.extra_tunnel;
+    dst.gamma = src.gamma;
+    dst.bond_i = src.bond_i;
+    dst.bond_j = src.bond_j;
+    dst.jump_kind = src.jump_kind;
+    dst.jump_site = src.jump_site;
+    dst.layout = src.layout;
+    dst.dim = (int64_t)keep.size();
+    dst.digits.resize((size_t)dst.dim * n);
+    dst.index.reserve((size_t)dst.dim * 2);
+    for (int64_t a = 0; a < dst.dim; ++a) {
+        std::copy(&src.digits[(size_t)keep[(size_t)a] * n], &src.digits[(size_t)keep[(size_t)a] * n] + n,
+                  &dst.digits[(size_t)a * n]);
+        dst.index.emplace(state_key(&dst.digits[(size_t)a * n], n), a);
+    }
+    // P H P and P A_j P: the entries between kept states, renumbered
+    for (const auto &e : src.h_entries) {
+        const int64_t r = to_new[(size_t)e.row], c = to_new[(size_t)e.col];
+        if (r >= 0 && c >= 0) dst.h_entries.push_back({r, c, e.unit, e.param, e.which});
+    }
+    dst.anti_diag.assign((size_t)dst.dim, 0.0);
+    for (const auto &e : src.jumps) {
+        const int64_t a = to_new[(size_t)e.src], b = to_new[(size_t)e.dst];
+        if (a < 0 || b < 0) continue;
+        dst.jumps.push_back({e.jump, a, b, e.coef});
+        dst.anti_diag[(size_t)a] += dst.gamma[(size_t)e.jump] * e.coef * e.coef;
+    }
+    return true;
+}
+
 double entry_coefficient(const HostModel &hm, const HostModel::HEntry &e) {
     switch (e.param) {
     case 1: return hm.g[e.which];

@@ -61,6 +61,12 @@ qed_status build_host_model(const qed_spec *spec, HostModel &hm, std::string &er
 
 std::string state_key(const uint8_t *digits, int n_digits);
 
+// The model on the basis states `keep` (increasing indices of src's basis): H and every
+// A_j projected onto them (P H P, P A_j P), renumbered; d_k recomputed from the kept jump
+// entries.  Returns false with `err` set for an empty or unsorted list.
+bool restrict_host_model(const HostModel &src, const std::vector<int64_t> &keep, HostModel &dst,
+                         std::string &err);
+
 // Dense row-major complex H.
 void dense_hamiltonian(const HostModel &hm, std::vector<cplx> &H);
 

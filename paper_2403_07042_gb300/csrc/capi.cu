@@ -251,6 +251,45 @@ int64_t next_multiple_after(int64_t off, int64_t i, int64_t every) {
     return i + (every - (off + i) % every);
 }
 
+// Device side of a model whose host model m->host is built: operators, tables, U, and
+// the split-precision state.  Synchronises `s`.
+qed_status build_device(qed_model *m, double dt, qed_precision prec, cudaStream_t s) {
+    m->D = m->host.dim;
+    m->dt = dt;
+    m->prec = prec;
+    const int64_t D = m->D;
+    const size_t DD = (size_t)(D * D);
+    QED_TRY(dev_alloc(&m->U, DD));
+    QED_TRY(dev_alloc(&m->work1, DD));
+    QED_TRY(dev_alloc(&m->work2, DD));
+    QED_TRY(dev_alloc(&m->scalars, 16));
+    QED_TRY(dev_alloc(&m->err, 1));
+    QED_CUDA_TRY(cudaMallocHost((void **)&m->err_host, sizeof(uint32_t)));
+    *m->err_host = 0;
+    QED_CUDA_TRY(cudaMemset(m->err, 0, sizeof(uint32_t)));
+    QED_TRY(upload_tables(m));
+    for (auto &e : m->ev) QED_CUDA_TRY(cudaEventCreate(&e));
+    // H into work1, then U = exp(-i H dt)
+    std::vector<cplx> Hd;
+    dense_hamiltonian(m->host, Hd);
+    double norm1 = 0.0;
+    for (int64_t c = 0; c < D; ++c) {
+        double col = 0.0;
+        for (int64_t r = 0; r < D; ++r) col += std::abs(Hd[(size_t)(r * D + c)]);
+        norm1 = std::max(norm1, col);
+    }
+    QED_CUDA_TRY(cudaMemcpyAsync(m->work1, Hd.data(), DD * 16, cudaMemcpyHostToDevice, s));
+    QED_TRY(propagator(s, D, dt, m->work1, norm1, m->U, m->err));
+    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
+    if (*m->err_host & kErrSingular) {
+        set_error("singular Pade denominator");
+        return QED_ENUMERIC;
+    }
+    if (prec != QED_FP64) QED_TRY(split_prepare(m, s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    return QED_OK;
+}
+
 }  // namespace
 
 }  // namespace qed
@@ -325,40 +364,7 @@ qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_st
     std::string err;
     qed_status st = build_host_model(spec, m->host, err, true);
     if (st != QED_OK) { set_error(err); return st; }
-    m->D = m->host.dim;
-    m->dt = dt;
-    m->prec = prec;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t D = m->D;
-    const size_t DD = (size_t)(D * D);
-    QED_TRY(dev_alloc(&m->U, DD));
-    QED_TRY(dev_alloc(&m->work1, DD));
-    QED_TRY(dev_alloc(&m->work2, DD));
-    QED_TRY(dev_alloc(&m->scalars, 16));
-    QED_TRY(dev_alloc(&m->err, 1));
-    QED_CUDA_TRY(cudaMallocHost((void **)&m->err_host, sizeof(uint32_t)));
-    *m->err_host = 0;
-    QED_CUDA_TRY(cudaMemset(m->err, 0, sizeof(uint32_t)));
-    QED_TRY(upload_tables(m.get()));
-    for (auto &e : m->ev) QED_CUDA_TRY(cudaEventCreate(&e));
-    // H into work1, then U = exp(-i H dt)
-    std::vector<cplx> Hd;
-    dense_hamiltonian(m->host, Hd);
-    double norm1 = 0.0;
-    for (int64_t c = 0; c < D; ++c) {
-        double col = 0.0;
-        for (int64_t r = 0; r < D; ++r) col += std::abs(Hd[(size_t)(r * D + c)]);
-        norm1 = std::max(norm1, col);
-    }
-    QED_CUDA_TRY(cudaMemcpyAsync(m->work1, Hd.data(), DD * 16, cudaMemcpyHostToDevice, s));
-    QED_TRY(propagator(s, D, dt, m->work1, norm1, m->U, m->err));
-    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
-    if (*m->err_host & kErrSingular) {
-        set_error("singular Pade denominator");
-        return QED_ENUMERIC;
-    }
-    if (prec != QED_FP64) QED_TRY(split_prepare(m.get(), s));
-    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    QED_TRY(build_device(m.get(), dt, prec, (cudaStream_t)stream));
     *out = m.release();
     return QED_OK;
 }
@@ -608,6 +614,94 @@ qed_status qed_get_U(const qed_model *m, void *U, qed_stream stream) {
     if (!m || !U) return einval("NULL argument");
     QED_CUDA_TRY(cudaMemcpyAsync(U, m->U, (size_t)(m->D * m->D) * 16, cudaMemcpyDeviceToDevice,
                                  (cudaStream_t)stream));
+    return QED_OK;
+}
+
+qed_status qed_select_states(qed_model *m, const void *rho0, int64_t steps_per_round, int32_t n_rounds, double eps,
+                             qed_model **out_model, void *rho_out, int64_t *keep, int64_t *n_keep, int64_t *sizes,
+                             qed_stream stream) {
+    if (!m || !rho0 || !out_model || !rho_out || !keep || !n_keep) return einval("NULL argument");
+    if (steps_per_round <= 0 || n_rounds <= 0 || !(eps >= 0.0)) return einval("bad selection parameters");
+    *out_model = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    using Owned = std::unique_ptr<qed_model, void (*)(qed_model *)>;
+    Owned owned(nullptr, release);  // the current reduced model, once one exists
+    qed_model *cur = m;
+    const int64_t D0 = m->D;
+    double2 *rho = nullptr, *rho_next = nullptr;
+    double *p0 = nullptr, *p1 = nullptr;
+    int32_t *flag = nullptr;
+    int64_t *idx = nullptr;
+    struct Free {
+        std::vector<void *> p;
+        ~Free() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } guard;
+    QED_TRY(dev_alloc(&rho, (size_t)(D0 * D0)));
+    guard.p.push_back(rho);
+    QED_TRY(dev_alloc(&rho_next, (size_t)(D0 * D0)));
+    guard.p.push_back(rho_next);
+    QED_TRY(dev_alloc(&p0, (size_t)D0));
+    guard.p.push_back(p0);
+    QED_TRY(dev_alloc(&p1, (size_t)D0));
+    guard.p.push_back(p1);
+    QED_TRY(dev_alloc(&flag, (size_t)D0));
+    guard.p.push_back(flag);
+    QED_TRY(dev_alloc(&idx, (size_t)D0));
+    guard.p.push_back(idx);
+    QED_CUDA_TRY(cudaMemcpyAsync(rho, rho0, (size_t)(D0 * D0) * 16, cudaMemcpyDeviceToDevice, s));
+    std::vector<int64_t> global((size_t)D0);
+    for (int64_t k = 0; k < D0; ++k) global[(size_t)k] = k;
+    std::vector<int32_t> hflag((size_t)D0);
+    const double inv_T = 1.0 / ((double)steps_per_round * m->dt);
+    for (int32_t r = 0; r < n_rounds; ++r) {
+        const int64_t D = cur->D;
+        // solve, then the growth speed of every probability over the round
+        diag_f64(s, D, rho, p0);
+        QED_TRY(qed_evolve(cur, rho, steps_per_round, 0, 0, 0, nullptr, nullptr, stream));
+        QED_TRY(qed_sync_status(cur, stream));
+        diag_f64(s, D, rho, p1);
+        select_states_flags(s, D, p0, p1, inv_T, eps, flag);
+        QED_CUDA_TRY(cudaMemcpyAsync(hflag.data(), flag, (size_t)D * 4, cudaMemcpyDeviceToHost, s));
+        QED_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int64_t> local;
+        for (int64_t k = 0; k < D; ++k)
+            if (hflag[(size_t)k]) local.push_back(k);
+        if (local.empty()) {
+            set_error("qed_select_states: every state fell below eps");
+            return QED_ENUMERIC;
+        }
+        const int64_t n = (int64_t)local.size();
+        if (sizes) sizes[r] = n;
+        if (n < D || (r == n_rounds - 1 && !owned)) {
+            // the remaining states: rho restricted to them, and the model on them (P H P, P A_j P)
+            QED_CUDA_TRY(cudaMemcpyAsync(idx, local.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+            gather_submatrix(s, D, rho, n, idx, rho_next);
+            std::swap(rho, rho_next);
+            Owned next(new qed_model(), release);
+            std::string err;
+            if (!restrict_host_model(cur->host, local, next->host, err)) return einval(err);
+            QED_TRY(build_device(next.get(), cur->dt, cur->prec, s));
+            next->renorm_every = cur->renorm_every;
+            if (cur->scheme != QED_SCHEME_LIE) QED_TRY(qed_set_scheme(next.get(), cur->scheme));
+            std::vector<int64_t> g2((size_t)n);
+            for (int64_t a = 0; a < n; ++a) g2[(size_t)a] = global[(size_t)local[(size_t)a]];
+            global.swap(g2);
+            owned = std::move(next);
+            cur = owned.get();
+        }
+        // normalise (and symmetrise) the density matrix of the remaining states
+        renormalise(s, n, rho, cur->scalars, cur->err);
+        QED_TRY(qed_sync_status(cur, stream));
+    }
+    const int64_t n = cur->D;
+    QED_CUDA_TRY(cudaMemcpyAsync(rho_out, rho, (size_t)(n * n) * 16, cudaMemcpyDeviceToDevice, s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    std::copy(global.begin(), global.end(), keep);
+    *n_keep = n;
+    *out_model = owned.release();
     return QED_OK;
 }
 

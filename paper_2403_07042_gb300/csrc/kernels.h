@@ -61,6 +61,13 @@ void lindblad_axpy_f64(cudaStream_t s, int64_t D, const double2 *X, const double
                        const double *anti, const int32_t *in_ptr, const int32_t *in_jump, const int32_t *in_src,
                        const double *in_coef, double tau);
 
+// State space selection (Sec. 3.2): p = Re diag(rho); keep[k] = (|p1 - p0|_k / T >= eps or
+// p1_k >= eps); out = rho[idx][:, idx] (n x n).
+void diag_f64(cudaStream_t s, int64_t D, const double2 *rho, double *p);
+void select_states_flags(cudaStream_t s, int64_t D, const double *p0, const double *p1, double inv_T, double eps,
+                         int32_t *keep);
+void gather_submatrix(cudaStream_t s, int64_t D, const double2 *rho, int64_t n, const int64_t *idx, double2 *out);
+
 // out[o] = rho_kk (id < D), or sum_k w[id-D][k] rho_kk; deterministic block reduction.
 void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights,
                  const int32_t *ids, int32_t n_obs, double *out);

@@ -296,6 +296,30 @@ __global__ void lindblad_axpy_f64_kernel(int64_t D, const double2 *__restrict__ 
     out[m * D + n] = make_double2(fma(tau, l.x, base.x), fma(tau, l.y, base.y));
 }
 
+// p[k] = Re rho_kk
+__global__ void diag_kernel(int64_t D, const double2 *rho, double *p) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < D) p[k] = rho[k * D + k].x;
+}
+
+// keep[k] = 1 if the probability's growth speed |p1 - p0| / T or the probability itself
+// is at least eps (state space selection, Sec. 3.2)
+__global__ void select_kernel(int64_t D, const double *p0, const double *p1, double inv_T, double eps,
+                              int32_t *keep) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= D) return;
+    const double growth = fabs(p1[k] - p0[k]) * inv_T;
+    keep[k] = (growth >= eps || p1[k] >= eps) ? 1 : 0;
+}
+
+// out[a][b] = rho[idx[a]][idx[b]] (n x n from D x D)
+__global__ void gather_kernel(int64_t D, const double2 *rho, int64_t n, const int64_t *idx, double2 *out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int64_t a = e / n, b = e % n;
+    out[e] = rho[idx[a] * D + idx[b]];
+}
+
 __global__ void dissipate_f64_kernel(int64_t D, const double2 *__restrict__ V, double2 *__restrict__ rho,
                                      const double *__restrict__ anti, const int32_t *__restrict__ in_ptr,
                                      const int32_t *__restrict__ in_jump, const int32_t *__restrict__ in_src,
@@ -484,6 +508,22 @@ void lindblad_axpy_f64(cudaStream_t s, int64_t D, const double2 *X, const double
     dim3 block(32, 8);
     dim3 grid(blocks_for(D, 32), blocks_for(D, 8));
     lindblad_axpy_f64_kernel<<<grid, block, 0, s>>>(D, X, B, out, anti, in_ptr, in_jump, in_src, in_coef, tau);
+}
+
+void diag_f64(cudaStream_t s, int64_t D, const double2 *rho, double *p) {
+    count_launches(1);
+    diag_kernel<<<blocks_for(D, 256), 256, 0, s>>>(D, rho, p);
+}
+
+void select_states_flags(cudaStream_t s, int64_t D, const double *p0, const double *p1, double inv_T, double eps,
+                         int32_t *keep) {
+    count_launches(1);
+    select_kernel<<<blocks_for(D, 256), 256, 0, s>>>(D, p0, p1, inv_T, eps, keep);
+}
+
+void gather_submatrix(cudaStream_t s, int64_t D, const double2 *rho, int64_t n, const int64_t *idx, double2 *out) {
+    count_launches(1);
+    gather_kernel<<<blocks_for(n * n, 256), 256, 0, s>>>(D, rho, n, idx, out);
 }
 
 void observables(cudaStream_t s, int64_t D, const double2 *rho, const double *weights, const int32_t *ids,
