@@ -48,9 +48,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jch2_d36", "lattice_32x32_d2049", "batched_chains",
-                            "adjoint_lattice_24x24_d1153"],
+                            "adjoint_lattice_24x24_d1153", "selection_hb_shaped_d512"],
                    help="the default is the headline workload; the others are measured with --workload")
     p.add_argument("--instances", type=int, default=512, help="batched_chains: number of instances")
+    p.add_argument("--selection-eps", type=float, default=1e-20, help="selection workload: threshold")
+    p.add_argument("--selection-round", type=int, default=100, help="selection workload: steps per round")
     return p.parse_args()
 
 
@@ -415,7 +417,7 @@ def run_other(args):
                          "hist_128": np.histogram(dims, bins=range(0, 1153, 128))[0].tolist()}
     else:
         m = {"jch2_d36": W.jch_two_cavities, "lattice_32x32_d2049": W.lattice,
-             "adjoint_lattice_24x24_d1153": W.adjoint_lattice}[wl]()
+             "adjoint_lattice_24x24_d1153": W.adjoint_lattice, "selection_hb_shaped_d512": W.hb_shaped}[wl]()
         steps = args.qme_steps or m["n_steps"]
         gm = qed.Model(m, precision=prec, scheme=args.scheme)
         D = gm.dim
@@ -435,6 +437,21 @@ def run_other(args):
             def one():
                 gm.adjoint(rho0, steps, w, checkpoint_every=m["checkpoint_every"])
             unit = "adjoint QME steps/s"
+        elif wl == "selection_hb_shaped_d512":
+            # the whole trajectory as rounds of state space selection (Sec. 3.2)
+            per_round = args.selection_round
+            rounds = max(1, steps // per_round)
+            steps = rounds * per_round
+            final = {}
+
+            def one():
+                red, _, keep, sizes = qed.select_states(gm, rho0, per_round, rounds, args.selection_eps)
+                final["dim"] = int(red.dim)
+                final["sizes_first"] = [int(x) for x in sizes[:3]]
+                red.close()
+            unit = "QME steps/s"
+            extra["selection"] = {"eps": args.selection_eps, "steps_per_round": per_round, "rounds": rounds,
+                                  "result": final}
         else:
             r = m["record_every"]
             rec = torch.zeros((gm.n_records(steps, r), D), dtype=torch.float64, device=dev)
@@ -443,7 +460,8 @@ def run_other(args):
                 rho.copy_(rho0)
                 gm.evolve(rho, steps, record_every=r, obs_ids=list(range(D)), records=rec)
             unit = "QME steps/s"
-        flops = 16.0 * D ** 3
+        # the selection run's dimension shrinks as it goes: no per-step flop count
+        flops = 0.0 if wl == "selection_hb_shaped_d512" else 16.0 * D ** 3
         per_step_units = steps
         extra["dim"] = D
     for _ in range(args.warmup):
