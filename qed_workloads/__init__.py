@@ -144,6 +144,17 @@ def lattice(length=32, width=32, g=0.01, zeta=0.01, gamma=1e-3, dt=0.1, n_steps=
                   lattice=(length, width))
 
 
+def photon_plane(length=81, width=51, zeta=0.1, dt=0.1, n_steps=2000, record_every=100, start=(40, 0)):
+    """The photon-motion plane of Sec. 4.2 at the paper's size: one photon on a length x
+    width grid of cavities without atoms (basis |i>|j>, dim = area = 4131), closed (no
+    jumps), nearest-neighbour hopping zeta; start (40, 0) is the paper's symmetric initial
+    state, (20, 0) its asymmetric one."""
+    m = lattice(length, width, zeta=zeta, gamma=0.0, dt=dt, n_steps=n_steps, record_every=record_every,
+                start=start, atoms=False, basis_kind=4)
+    m["name"] = f"photon_plane_{length}x{width}"
+    return m
+
+
 def _product_dim(L, k, n):
     return ((n + 1) * 2 ** k) ** L
 

@@ -27,3 +27,19 @@ def lattice_single_excitation_state(L, Wd, omega, g, zeta, t, start):
     psi[1::2] = photon.reshape(-1)
     psi[2::2] = atom.reshape(-1)
     return psi
+
+
+def plane_photon_state(L, Wd, omega, zeta, t, start):
+    """One photon on an L x Wd grid of cavities without atoms (open boundaries): the hopping
+    matrix has the separable modes phi_p(i) phi_q(j), phi_p(i) = sqrt(2/(n+1)) sin(k_p (i+1)),
+    k_p = pi p/(n+1), energies omega + 2 zeta (cos k_p + cos k_q).  Returns the amplitude
+    grid psi[i, j] at time t from the photon in cavity `start`."""
+    def modes(n):
+        k = np.pi * np.arange(1, n + 1) / (n + 1)
+        return np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(np.arange(1, n + 1), k)), k
+    phi_i, ki = modes(L)
+    phi_j, kj = modes(Wd)
+    i0, j0 = start
+    e = omega + 2 * zeta * (np.cos(ki)[:, None] + np.cos(kj)[None, :])
+    w = phi_i[i0][:, None] * phi_j[j0][None, :] * np.exp(-1j * e * t)
+    return phi_i @ w @ phi_j.T

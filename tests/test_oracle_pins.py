@@ -530,3 +530,22 @@ def test_selection_rounds_normalise_and_shrink():
     assert abs(np.trace(rho).real - 1.0) < 1e-14
     assert np.abs(rho - rho.conj().T).max() < 1e-15
     assert oracle.initial_index(m, b) in keep
+
+
+def test_photon_plane_closed_form():
+    """One photon on a 9 x 5 plane without atoms (Sec. 4.2, basis |i>|j>): the oracle's
+    trajectory equals the separable open-boundary mode expansion, and the symmetric start
+    (4, 0) keeps the mirror symmetry P(i, j) = P(8 - i, j)."""
+    from closed_forms import plane_photon_state
+    m = W.photon_plane(9, 5, zeta=0.1, dt=0.1, n_steps=300, start=(4, 0))
+    b = oracle.enumerate_basis(m)
+    assert b.dim == 45
+    rho = oracle.evolve(m, basis=b, return_records=False)
+    psi = plane_photon_state(9, 5, 1.0, 0.1, 30.0, (4, 0))
+    cav = np.array([int(np.flatnonzero(d)[0]) for d in b.digits])   # cavity of each basis state
+    amp = psi.reshape(-1)[cav]
+    assert np.abs(rho - np.outer(amp, amp.conj())).max() < 1e-12
+    P = np.zeros(45)
+    P[cav] = np.real(np.diag(rho))
+    P = P.reshape(9, 5)
+    assert np.abs(P - P[::-1, :]).max() < 1e-13
