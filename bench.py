@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jch2_d36", "lattice_32x32_d2049", "batched_chains",
-                            "adjoint_lattice_24x24_d1153", "selection_hb_shaped_d512"],
+                            "adjoint_lattice_24x24_d1153", "selection_hb_shaped_d512", "photon_plane_81x51_d4131"],
                    help="the default is the headline workload; the others are measured with --workload")
     p.add_argument("--instances", type=int, default=512, help="batched_chains: number of instances")
     p.add_argument("--selection-eps", type=float, default=1e-20, help="selection workload: threshold")
@@ -417,7 +417,8 @@ def run_other(args):
                          "hist_128": np.histogram(dims, bins=range(0, 1153, 128))[0].tolist()}
     else:
         m = {"jch2_d36": W.jch_two_cavities, "lattice_32x32_d2049": W.lattice,
-             "adjoint_lattice_24x24_d1153": W.adjoint_lattice, "selection_hb_shaped_d512": W.hb_shaped}[wl]()
+             "adjoint_lattice_24x24_d1153": W.adjoint_lattice, "selection_hb_shaped_d512": W.hb_shaped,
+             "photon_plane_81x51_d4131": W.photon_plane}[wl]()
         steps = args.qme_steps or m["n_steps"]
         gm = qed.Model(m, precision=prec, scheme=args.scheme)
         D = gm.dim

@@ -93,3 +93,34 @@ def test_lattice_fp64_and_split_short_vs_oracle():
         gm.evolve(rho, 20)
         gm.sync()
         assert np.abs(rho.cpu().numpy() - rho_ref).max() <= tol, prec
+
+
+@pytest.mark.parametrize("start,steps", [((40, 0), 1000), ((20, 0), 500)])
+def test_photon_plane_81x51_paper_size_split(start, steps):
+    """The paper's plane (Sec. 4.2: length 81, height 51, area 4131, one photon, symmetric
+    start (40, 0) and asymmetric start (20, 0)) on the split-precision path against the
+    separable closed form; the symmetric start keeps P(i, j) = P(80 - i, j)."""
+    from closed_forms import plane_photon_state
+    m = W.photon_plane(start=start)
+    gm = qed.Model(m, precision="split_fp16x2")
+    D = gm.dim
+    assert D == 4131
+    cav = np.array([int(np.flatnonzero(d)[0]) for d in gm.labels()])  # cavity of each basis state
+    i0 = gm.initial_index()
+    rho = torch.zeros((D, D), dtype=torch.complex128, device="cuda")
+    rho[i0, i0] = 1.0
+    gm.evolve(rho, steps)
+    gm.sync()
+    r = rho.cpu().numpy()
+    amp = plane_photon_state(81, 51, 1.0, m["zeta"][0], m["dt"] * steps, start).reshape(-1)[cav]
+    pop_err = np.abs(np.real(np.diag(r)) - np.abs(amp) ** 2).max()
+    rows = [0, i0, D // 2, D - 1]
+    rho_err = np.abs(r[rows] - np.outer(amp[rows], amp.conj())).max()
+    print(f"plane 81x51 from {start}, {steps} steps: max|dpop|={pop_err:.2e} max|drho| (rows)={rho_err:.2e}")
+    assert pop_err <= 1e-6 and rho_err <= 1e-5
+    assert abs(np.trace(r).real - 1.0) <= 1e-7
+    if start == (40, 0):
+        P = np.zeros(D)
+        P[cav] = np.real(np.diag(r))
+        P = P.reshape(81, 51)
+        assert np.abs(P - P[::-1, :]).max() <= 1e-6
