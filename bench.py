@@ -420,7 +420,10 @@ def run_other(args):
              "adjoint_lattice_24x24_d1153": W.adjoint_lattice, "selection_hb_shaped_d512": W.hb_shaped,
              "photon_plane_81x51_d4131": W.photon_plane}[wl]()
         steps = args.qme_steps or m["n_steps"]
+        t_build = time.perf_counter()
         gm = qed.Model(m, precision=prec, scheme=args.scheme)
+        # basis, operators and U = exp(-i H dt) (the "Taylor approximation" stage of Table 3)
+        extra["model_build_s"] = time.perf_counter() - t_build
         D = gm.dim
         rho0 = torch.zeros((D, D), dtype=torch.complex128, device=dev)
         i0 = gm.initial_index()
