@@ -446,7 +446,7 @@ bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_p
     // split-K slices (a power of two <= 4) while the tiles fill fewer
     // than half the SMs and each slice keeps at least 4 k-blocks
     int splits = 1;
-    while (splits < 4 && tiles * splits * 2 <= num_sms && kb_total / (splits * 2) >= 4) splits *= 2;
+    while (splits < kTcMaxAutoSplits && tiles * splits * 2 <= num_sms && kb_total / (splits * 2) >= 4) splits *= 2;
     if (force_splits > 0) splits = force_splits > kb_total ? kb_total : force_splits;
     g.kb_per_split = (kb_total + splits - 1) / splits;
     g.splits = (kb_total + g.kb_per_split - 1) / g.kb_per_split;

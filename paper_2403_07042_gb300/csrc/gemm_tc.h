@@ -29,6 +29,9 @@ struct TcGemm {
 };
 
 constexpr int kTcBM = 128;
+// The planner splits K into at most this many slices (the element-wise kernels that sum
+// the slices of the step's products hold that many loads in flight).
+constexpr int kTcMaxAutoSplits = 4;
 // Tile widths: 128 x 256 x 16 instructions run near the SM's tensor peak, 128 x 128 x 16 at
 // about half, but small products need the narrower tiles to spread over the SMs.
 constexpr int kTcBNMax = 256;

@@ -56,8 +56,8 @@ struct InstDesc {
 // entry, all gathers in flight together) instead of the two-pointer merge of the lists.
 constexpr int kInMax = 4;
 constexpr int kNoJump = 0x7fffffff;
-// Split-K slices the element-wise kernels sum (the plan caps them at 4).
-constexpr int kMaxSlices = 4;
+// Split-K slices the element-wise kernels sum (the plan's cap).
+constexpr int kMaxSlices = kTcMaxAutoSplits;
 
 // 32 x 32 tiles of W (w_reduce) or 32 x 8 element blocks (form_v, dissipate) of one instance
 struct TileItem {
