@@ -262,6 +262,57 @@ __global__ void take_right_half_kernel(int64_t D, const double2 *aug, double2 *R
     R[idx] = aug[(idx / D) * 2 * D + D + idx % D];
 }
 
+// Pairs of long incoming lists (many jumps into one state, e.g. every leak into the
+// vacuum): the whole warp (blockDim.x == 32, every lane present) merges each such pair.
+// Lanes take every 32nd entry of the shorter list and find its jump in the longer one by
+// bisection; the owner lane of the pair gets scale * sum c_p c_q X[src_p, src_q] added to
+// acc.  Returns whether this lane's own pair was handled here.
+constexpr int kLongMergeF64 = 32;
+
+__device__ bool long_merge_f64(int64_t D, const double2 *X, const int32_t *in_jump, const int32_t *in_src,
+                               const double *in_coef, int p, int pe, int q, int qe, double scale, double2 &acc) {
+    const bool is_long = pe > p && qe > q && (pe - p) + (qe - q) > kLongMergeF64;
+    unsigned longs = __ballot_sync(0xffffffffu, is_long);
+    const int lane = threadIdx.x;
+    while (longs) {
+        const int owner = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int op = __shfl_sync(0xffffffffu, p, owner), ope = __shfl_sync(0xffffffffu, pe, owner);
+        const int oq = __shfl_sync(0xffffffffu, q, owner), oqe = __shfl_sync(0xffffffffu, qe, owner);
+        const bool m_short = ope - op <= oqe - oq;
+        const int s0 = m_short ? op : oq, s1 = m_short ? ope : oqe;
+        const int l0 = m_short ? oq : op, l1 = m_short ? oqe : ope;
+        double sx = 0.0, sy = 0.0;
+        for (int e = s0 + lane; e < s1; e += 32) {
+            const int j = in_jump[e];
+            int lo = l0, hi = l1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (in_jump[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo < l1 && in_jump[lo] == j) {
+                const int ep = m_short ? e : lo, eq = m_short ? lo : e;
+                const double c = scale * in_coef[ep] * in_coef[eq];
+                const double2 g = X[(int64_t)in_src[ep] * D + in_src[eq]];
+                sx = fma(c, g.x, sx);
+                sy = fma(c, g.y, sy);
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, off);
+            sy += __shfl_xor_sync(0xffffffffu, sy, off);
+        }
+        if (lane == owner) {
+            acc.x += sx;
+            acc.y += sy;
+        }
+    }
+    return is_long;
+}
+
 // out = B + tau [ -(d_m + d_n)/2 X_mn + sum_j c_j(m) c_j(n) X[src_j(m), src_j(n)] ]: a stage
 // of the explicit midpoint rule for the Lindblad term (Eq. 3).  out may be B (each
 // element reads only its own B entry), never X.
@@ -271,12 +322,14 @@ __global__ void lindblad_axpy_f64_kernel(int64_t D, const double2 *__restrict__ 
                                          const double *__restrict__ in_coef, double tau) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    if (m >= D || n >= D) return;
-    const double2 x = X[m * D + n];
-    const double h = -0.5 * (anti[m] + anti[n]);
+    const bool inside = m < D && n < D;  // outside lanes stay for the warp-shared merge
+    const int64_t mc = inside ? m : 0, nc = inside ? n : 0;
+    const double2 x = X[mc * D + nc];
+    const double h = -0.5 * (anti[mc] + anti[nc]);
     double2 l = make_double2(h * x.x, h * x.y);
-    int a = in_ptr[m], ae = in_ptr[m + 1];
-    int b = in_ptr[n], be = in_ptr[n + 1];
+    int a = inside ? in_ptr[m] : 0, ae = inside ? in_ptr[m + 1] : 0;
+    int b = inside ? in_ptr[n] : 0, be = inside ? in_ptr[n + 1] : 0;
+    if (long_merge_f64(D, X, in_jump, in_src, in_coef, a, ae, b, be, 1.0, l)) ae = a;
     while (a < ae && b < be) {  // jumps present in both incoming lists
         const int ja = in_jump[a], jb = in_jump[b];
         if (ja < jb) {
@@ -292,6 +345,7 @@ __global__ void lindblad_axpy_f64_kernel(int64_t D, const double2 *__restrict__ 
             ++b;
         }
     }
+    if (!inside) return;
     const double2 base = B[m * D + n];
     out[m * D + n] = make_double2(fma(tau, l.x, base.x), fma(tau, l.y, base.y));
 }
@@ -326,12 +380,14 @@ __global__ void dissipate_f64_kernel(int64_t D, const double2 *__restrict__ V, d
                                      const double *__restrict__ in_coef, double dt) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t m = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
-    if (m >= D || n >= D) return;
-    double2 v = V[m * D + n];
-    double f = 1.0 - 0.5 * dt * (anti[m] + anti[n]);
+    const bool inside = m < D && n < D;  // outside lanes stay for the warp-shared merge
+    const int64_t mc = inside ? m : 0, nc = inside ? n : 0;
+    double2 v = V[mc * D + nc];
+    double f = 1.0 - 0.5 * dt * (anti[mc] + anti[nc]);
     double2 out = make_double2(v.x * f, v.y * f);
-    int a = in_ptr[m], ae = in_ptr[m + 1];
-    int b = in_ptr[n], be = in_ptr[n + 1];
+    int a = inside ? in_ptr[m] : 0, ae = inside ? in_ptr[m + 1] : 0;
+    int b = inside ? in_ptr[n] : 0, be = inside ? in_ptr[n + 1] : 0;
+    if (long_merge_f64(D, V, in_jump, in_src, in_coef, a, ae, b, be, dt, out)) ae = a;
     while (a < ae && b < be) {  // jumps present in both incoming lists
         int ja = in_jump[a], jb = in_jump[b];
         if (ja < jb) {
@@ -347,6 +403,7 @@ __global__ void dissipate_f64_kernel(int64_t D, const double2 *__restrict__ V, d
             ++b;
         }
     }
+    if (!inside) return;
     rho[m * D + n] = out;
 }
 

@@ -56,6 +56,8 @@ struct InstDesc {
 // entry, all gathers in flight together) instead of the two-pointer merge of the lists.
 constexpr int kInMax = 4;
 constexpr int kNoJump = 0x7fffffff;
+// Pairs of incoming lists longer than this in total are merged by the whole warp.
+constexpr int kLongMerge = 32;
 // Split-K slices the element-wise kernels sum (the plan's cap).
 constexpr int kMaxSlices = kTcMaxAutoSplits;
 
@@ -362,6 +364,59 @@ __device__ __forceinline__ float4 *state_buf(const InstDesc &a, int sel) {
     return sel == 0 ? a.rho : (sel == 1 ? a.V : a.Y);
 }
 
+// A pair of long incoming lists (many jumps into one state, e.g. every leak into the
+// vacuum): the whole warp (blockDim.x == 32, every lane present) shares the merge of each
+// such pair.  Lanes take every 32nd entry of the shorter list and find its jump in the
+// longer one by bisection; the owner lane gets the sum of c_p c_q X[src_p, src_q] (dt
+// included in the coefficients) added to (gr, gi).  Returns whether this lane's own pair
+// was handled.  Kept out of line so that the common path keeps its registers.
+__device__ __noinline__ bool long_merge_df(int64_t D, const int32_t *in_jump, const int32_t *in_src,
+                                           const float2 *coef, const float4 *X, int p, int pe, int q, int qe,
+                                           float &gr, float &gi) {
+    const bool is_long = pe > p && qe > q && (pe - p) + (qe - q) > kLongMerge;
+    unsigned longs = __ballot_sync(0xffffffffu, is_long);
+    const int lane = threadIdx.x;
+    while (longs) {
+        const int owner = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int op = __shfl_sync(0xffffffffu, p, owner), ope = __shfl_sync(0xffffffffu, pe, owner);
+        const int oq = __shfl_sync(0xffffffffu, q, owner), oqe = __shfl_sync(0xffffffffu, qe, owner);
+        const bool m_short = ope - op <= oqe - oq;
+        const int s0 = m_short ? op : oq, s1 = m_short ? ope : oqe;
+        const int l0 = m_short ? oq : op, l1 = m_short ? oqe : ope;
+        float sr = 0.f, si = 0.f;
+        for (int e = s0 + lane; e < s1; e += 32) {
+            const int j = in_jump[e];
+            int lo = l0, hi = l1;  // first entry of the longer list with jump >= j
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (in_jump[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo < l1 && in_jump[lo] == j) {
+                const int ep = m_short ? e : lo, eq = m_short ? lo : e;  // row m's entry, row n's
+                const float2 cp = coef[ep], cq = coef[eq];
+                const df c = df_mul({cp.x, cp.y}, {cq.x, cq.y});
+                const float4 u = X[(int64_t)in_src[ep] * D + in_src[eq]];
+                const float ur = u.x + u.y, ui = u.z + u.w;
+                sr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, sr));
+                si = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, si));
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, off);
+            si += __shfl_xor_sync(0xffffffffu, si, off);
+        }
+        if (lane == owner) {
+            gr += sr;
+            gi += si;
+        }
+    }
+    return is_long;
+}
+
 template <bool LIE>
 __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ tiles,
                                                 const InstDesc *__restrict__ descs, int xsel, int bsel, int osel,
@@ -387,8 +442,9 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     float4 *O = LIE ? a.rho : state_buf(a, osel);
     pdl_wait();
     pdl_trigger();
-    if (!inside) return;
-    const cdf v = load_cdf(X[m * D + n]);
+    // lanes outside the matrix stay to the end (with clamped indices, no stores): the warp
+    // shares the merge of long jump lists below
+    const cdf v = load_cdf(X[mc * D + nc]);
     if (a.in_tab) {
 #pragma unroll
         for (int i = 0; i < kInMax; ++i) en[i] = a.in_tab[nc * kInMax + i];
@@ -426,8 +482,14 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
             gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
         }
     }
-    int p = a.in_tab ? 0 : a.in_ptr[m], pe = a.in_tab ? 0 : a.in_ptr[m + 1];
-    int q = a.in_tab ? 0 : a.in_ptr[n], qe = a.in_tab ? 0 : a.in_ptr[n + 1];
+    const bool lists = !a.in_tab && inside;
+    int p = lists ? a.in_ptr[m] : 0, pe = lists ? a.in_ptr[m + 1] : 0;
+    int q = lists ? a.in_ptr[n] : 0, qe = lists ? a.in_ptr[n + 1] : 0;
+    if (!a.in_tab) {
+        // long lists: merged by the whole warp
+        const bool is_long = long_merge_df(D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
+        if (is_long) pe = p;  // done: skip the serial merge
+    }
     while (p < pe && q < qe) {  // jumps present in both incoming lists
         const int jp = a.in_jump[p], jq = a.in_jump[q];
         if (jp < jq) {
@@ -445,6 +507,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
             ++q;
         }
     }
+    if (!inside) return;
     const cdf b = LIE ? v : load_cdf(B[m * D + n]);
     cdf out;
     out.re = df_add_f(b.re, LIE ? gr : f * gr);
