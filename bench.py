@@ -115,6 +115,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest replica's time (ms): the whole job finishes when its slowest rank does."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units per second of all replicas together (each rank runs units_per_rank)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -234,12 +250,8 @@ def run_ours(args):
     clocks = sampler.stop()
     gm.sync()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = t_ms
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps * qme_steps / (t_max / 1e3)
+    t_max = max_over_ranks(t_ms, world, dev)
+    value = whole_job_rate(world, args.steps * qme_steps, t_max)
 
     # parity of this run's final state against the stored oracle trajectory, if present
     parity = parity_against_golden(rho, records, qme_steps) if args.scheme == "lie" else None
@@ -261,17 +273,15 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * args.steps * qme_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = whole_job_rate(world, args.steps * qme_steps, e2e_ms)
 
     # kernel classes timed live with CUDA events on the launching stream
     prof_steps = min(500, qme_steps)
     rho.copy_(rho0)
     kern = gm.profile(rho, prof_steps)
     roofline = make_roofline(kern, D, args.precision)
+    roofline_dissipator = dissipator_roofline(kern, D)
 
     # the all-FP64 GPU path on the same workload (shorter run)
     fp64 = None
@@ -314,6 +324,7 @@ def run_ours(args):
         "parity_vs_oracle": parity,
         "fp64_gpu": fp64,
         "roofline": roofline,
+        "roofline_dissipator": roofline_dissipator,
         "kernels_ms_per_qme_step": kern,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "QME steps/s", "h2d_bytes_per_step": step_bytes_in,
@@ -324,6 +335,21 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def dissipator_roofline(kern, D):
+    """The Lindblad update's achieved bandwidth against the measured HBM copy rate: the
+    algorithmic bytes are the element's V read (16 B), the new rho written (16 B) and its
+    FP16 planes written (8 B), per complex element (the gathers of the jump terms come on
+    top).  Its operands sit in L2 at these sizes, so the fraction is a lower bound of what the
+    memory system delivers."""
+    name = "dissipate" if "dissipate" in kern else ("dissipate_f64" if "dissipate_f64" in kern else None)
+    if not name or kern[name] <= 0:
+        return None
+    peaks, src = measured_peaks()
+    achieved = 40.0 * D * D / (kern[name] * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "bytes_per_element": 40, "peak_source": src}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one GEMM1 launch (ncu, warm L2)
