@@ -48,7 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jch2_d36", "lattice_32x32_d2049", "batched_chains",
-                            "adjoint_lattice_24x24_d1153", "selection_hb_shaped_d512", "photon_plane_81x51_d4131"],
+                            "adjoint_lattice_24x24_d1153", "selection_hb_shaped_d512", "photon_plane_81x51_d4131",
+                            "hb_two_bonds_d4096"],
                    help="the default is the headline workload; the others are measured with --workload")
     p.add_argument("--instances", type=int, default=512, help="batched_chains: number of instances")
     p.add_argument("--selection-eps", type=float, default=1e-20, help="selection workload: threshold")
@@ -444,7 +445,7 @@ def run_other(args):
     else:
         m = {"jch2_d36": W.jch_two_cavities, "lattice_32x32_d2049": W.lattice,
              "adjoint_lattice_24x24_d1153": W.adjoint_lattice, "selection_hb_shaped_d512": W.hb_shaped,
-             "photon_plane_81x51_d4131": W.photon_plane}[wl]()
+             "photon_plane_81x51_d4131": W.photon_plane, "hb_two_bonds_d4096": W.hb_two_bonds}[wl]()
         steps = args.qme_steps or m["n_steps"]
         t_build = time.perf_counter()
         gm = qed.Model(m, precision=prec, scheme=args.scheme)

@@ -100,6 +100,23 @@ def hb_shaped(seed=0, n_steps=10000, record_every=100, gamma=1e-3, gamma_pos=1e-
                   init={"atoms": {0: 1}})
 
 
+def hb_two_bonds(seed=0, n_steps=3000, record_every=100, gamma=1e-3, gamma_pos=1e-4, tunnel=0.005):
+    """The size of the paper's two-hydrogen-bond model (Sec. 3.1: 12 binary digits, 2^12 =
+    4096 states, 3000 iterations): six two-level modes in two chains of three, an atom on
+    the outer modes of each chain, two tunnelling digits; seven jump operators (loss from
+    each mode, dephasing of the first tunnelling digit).  The paper prints neither its
+    parameters nor its operators; this model matches its dimension, digit count and number
+    of iterations."""
+    rng = np.random.default_rng(seed)
+    g = [float(x) for x in rng.uniform(0.005, 0.02, size=4)]
+    zeta = [float(x) for x in rng.uniform(0.002, 0.01, size=4)]
+    jumps = [(0, c, gamma) for c in range(6)] + [(2, 0, gamma_pos)]
+    return _model(name="hb_two_bonds_d4096", n_cavities=6, atoms_per_cavity=[1, 0, 1, 1, 0, 1], n_max=[1] * 6,
+                  n_extra=2, omega_c=1.0, omega_a=1.0, g=g, bonds=[(0, 1), (1, 2), (3, 4), (4, 5)], zeta=zeta,
+                  extra_tunnel=[tunnel, tunnel], jumps=jumps, dt=0.05, n_steps=n_steps,
+                  record_every=record_every, init={"atoms": {0: 1}})
+
+
 def _grid_bonds(length, width):
     """Nearest-neighbour edges of a length x width grid, cavity c = i * width + j."""
     bonds = []
