@@ -172,6 +172,7 @@ qed_status qed_set_scheme(qed_model *m, int32_t scheme);
  * Advance rho (device complex128 D x D, in/out) by n_steps steps of
  *     V = U rho U^+                          ("unitary evolution", Sec. 4.2, Eq. 2)
  *     rho <- V + dt sum_j gamma_j (A_j V A_j^+ - 1/2 {A_j^+ A_j, V})      (Eq. 3)
+ * (the Lie scheme; under QED_SCHEME_STRANG the symmetric step of qed_set_scheme).
  * Records observables obs_ids (host int32 [n_obs]) into records (device FP64,
  * row-major [n_rec x n_obs]) at every local step i in 0..n_steps (before step i+1)
  * with (step_offset + i) % record_every == 0; records may be NULL when n_obs == 0.
