@@ -617,7 +617,23 @@ def _trace_dissipator(lam, V, A):
     return sandwich - 0.5 * np.sum(K.data * (vl + lv))
 
 
-def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
+def _lindblad_midpoint_adjoint(Lam, jumps, tau):
+    """The Hilbert-Schmidt adjoint of lindblad_midpoint: Lam + tau L^+(T) with the stage
+    T = Lam + tau/2 L^+(Lam); returns (result, T)."""
+    T = Lam + 0.5 * tau * lindblad_adjoint(Lam, jumps)
+    return Lam + tau * lindblad_adjoint(T, jumps), T
+
+
+def _midpoint_rate_traces(Lam, T, Y, jumps, tau):
+    """d/dgamma_j of tr(Lam E(Y)) for the midpoint step E(Y) = Y + tau L Y + tau^2/2 L^2 Y,
+    L = sum_j gamma_j D_j: tr(Lam (tau D_j Y + tau^2/2 (D_j L Y + L D_j Y)))
+    = tau tr(T D_j(Y)) + tau^2/2 tr(Lam D_j(L Y)), T = Lam + tau/2 L^+(Lam)."""
+    LY = lindblad(Y, jumps)
+    return np.array([np.real(tau * _trace_dissipator(T, Y, A) + 0.5 * tau * tau * _trace_dissipator(Lam, LY, A))
+                     for _, A in jumps])
+
+
+def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None, scheme="lie"):
     """Discrete adjoint of L = tr(diag(obs) rho_N) through the map of `step`.
 
     lambda_N = O; lambda'_{n+1} = J^+(lambda_{n+1}) with J(V) = V + dt L(V);
@@ -625,7 +641,14 @@ def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
     dL/dgamma_j = dt * sum_n tr(lambda_{n+1} D_j(V_n)),
     dL/dtheta   = 2 Re sum_n tr(lambda'_{n+1} (dU/dtheta) rho_n U^+), with dU/dtheta from
     the Daleckii-Krein divided differences of exp(-i lambda dt) in H's eigenbasis.
+
+    scheme="strang": the map of step_strang, X_n = E(rho_n), V_n = U X_n U^+,
+    rho_{n+1} = E(V_n) with the midpoint half step E (tau = dt/2): kappa_n = E^+(lambda_{n+1}),
+    mu_n = U^+ kappa_n U, lambda_n = E^+(mu_n); M = sum_n X_n U^+ kappa_n; the rate gradients
+    differentiate both half steps (_midpoint_rate_traces).
     Returns (loss, grad_g, grad_zeta, grad_gamma)."""
+    if scheme == "strang":
+        return _adjoint_gradients_strang(model, obs_diag, n_steps, rho0, basis)
     basis = basis or enumerate_basis(model)
     H = hamiltonian(model, basis)
     dt = model["dt"]
@@ -651,6 +674,14 @@ def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
         lam_prime = lam_next + dt * lindblad_adjoint(lam_next, jumps)
         M += rhos[n] @ U.conj().T @ lam_prime
         lam_next = U.conj().T @ lam_prime @ U
+    grad_g, grad_zeta = _hamiltonian_gradients(model, basis, lam, Q, f, dt, M)
+    return loss, grad_g, grad_zeta, grad_gamma
+
+
+def _hamiltonian_gradients(model, basis, lam, Q, f, dt, M):
+    """dL/dtheta = 2 Re tr(dU/dtheta M) for every g and zeta, dU/dtheta by the
+    Daleckii-Krein divided differences of f(x) = exp(-i x dt) at H's eigenvalues lam
+    (eigenvectors Q, f = f(lam))."""
     # divided differences F_kl of f(x) = exp(-i x dt) at the eigenvalues
     dl = lam[:, None] - lam[None, :]
     same = np.abs(dl) < 1e-13 * max(1.0, float(np.max(np.abs(lam))))
@@ -665,6 +696,39 @@ def adjoint_gradients(model, obs_diag, n_steps=None, rho0=None, basis=None):
 
     grad_g = np.array([contract(("g", a)) for a in range(len(model["g"]))])
     grad_zeta = np.array([contract(("zeta", b)) for b in range(len(model["zeta"]))])
+    return grad_g, grad_zeta
+
+
+def _adjoint_gradients_strang(model, obs_diag, n_steps, rho0, basis):
+    basis = basis or enumerate_basis(model)
+    H = hamiltonian(model, basis)
+    dt = model["dt"]
+    tau = 0.5 * dt
+    n_steps = model["n_steps"] if n_steps is None else n_steps
+    lam, Q = np.linalg.eigh(H)
+    f = np.exp(-1j * lam * dt)
+    U = (Q * f) @ Q.conj().T
+    jumps = jump_operators(model, basis)
+    rho = initial_density(model, basis) if rho0 is None else np.array(rho0, dtype=np.complex128)
+    rhos = [rho]
+    for _ in range(n_steps):
+        rho = step_strang(rho, U, jumps, dt)
+        rhos.append(rho)
+    O = np.diag(np.asarray(obs_diag, dtype=float)).astype(np.complex128)
+    loss = float(np.real(np.trace(O @ rhos[-1])))
+    lam_next = O
+    M = np.zeros_like(H)
+    grad_gamma = np.zeros(len(jumps))
+    for n in reversed(range(n_steps)):
+        X = lindblad_midpoint(rhos[n], jumps, tau)
+        V = U @ X @ U.conj().T
+        kappa, T1 = _lindblad_midpoint_adjoint(lam_next, jumps, tau)
+        grad_gamma += _midpoint_rate_traces(lam_next, T1, V, jumps, tau)
+        M += X @ U.conj().T @ kappa
+        mu = U.conj().T @ kappa @ U
+        lam_next, T2 = _lindblad_midpoint_adjoint(mu, jumps, tau)
+        grad_gamma += _midpoint_rate_traces(mu, T2, rhos[n], jumps, tau)
+    grad_g, grad_zeta = _hamiltonian_gradients(model, basis, lam, Q, f, dt, M)
     return loss, grad_g, grad_zeta, grad_gamma
 
 
@@ -686,7 +750,7 @@ def loss_diag(model, basis, photons=(), atoms=()):
     return w
 
 
-def loss_value(model, obs_diag, params=None, n_steps=None, basis=None):
+def loss_value(model, obs_diag, params=None, n_steps=None, basis=None, scheme="lie"):
     """tr(diag(obs) rho_N) with some parameters overridden: used by finite differences."""
     m = dict(model)
     if params:
@@ -695,5 +759,5 @@ def loss_value(model, obs_diag, params=None, n_steps=None, basis=None):
             arr = list(m[key])
             arr[i] = v
             m[key] = arr
-    rho = evolve(m, n_steps=n_steps, basis=basis, return_records=False)
+    rho = evolve(m, n_steps=n_steps, basis=basis, return_records=False, scheme=scheme)
     return float(np.real(np.sum(np.asarray(obs_diag) * np.diag(rho))))

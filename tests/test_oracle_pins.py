@@ -549,3 +549,61 @@ def test_photon_plane_closed_form():
     P[cav] = np.real(np.diag(rho))
     P = P.reshape(9, 5)
     assert np.abs(P - P[::-1, :]).max() < 1e-13
+
+
+def test_strang_adjoint_matches_central_differences():
+    """The discrete adjoint of the Strang step against the fourth-order central stencil
+    (h = 1e-3) for couplings, hoppings and a leak rate of a 3 x 3 lattice, and for photon
+    loss, atom decay and dephasing rates of a two-cavity model from a random mixed state."""
+    h = 1e-3
+
+    def stencil(f):
+        return (-f(2 * h) + 8 * f(h) - 8 * f(-h) + f(-2 * h)) / (12 * h)
+
+    m = W.lattice(3, 3, seed=4, gamma=0.02, dt=0.1, n_steps=60, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    loss, gg, gz, gga = oracle.adjoint_gradients(m, w, basis=b, scheme="strang")
+    assert abs(loss - oracle.loss_value(m, w, basis=b, scheme="strang")) < 1e-14
+    for name, i, grad in (("g", 0, gg[0]), ("g", 4, gg[4]), ("zeta", 0, gz[0]), ("zeta", 5, gz[5])):
+        base = m[name][i]
+        fd = stencil(lambda d: oracle.loss_value(m, w, {(name, i): base + d}, basis=b, scheme="strang"))
+        assert abs(grad - fd) <= 1e-6 * abs(fd) + 1e-10, (name, i, grad, fd)
+    j = 3
+
+    def with_rate(d):
+        jumps = [(k, s, g + (d if q == j else 0.0)) for q, (k, s, g) in enumerate(m["jumps"])]
+        return oracle.loss_value(dict(m, jumps=jumps), w, basis=b, scheme="strang")
+    fd = stencil(with_rate)
+    assert abs(gga[j] - fd) <= 1e-6 * abs(fd) + 1e-10
+
+    m2 = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m2.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+              zeta=[0.006], dt=0.1)
+    m2["jumps"] = list(m2["jumps"]) + [(1, 0, 0.01)]
+    b2 = oracle.enumerate_basis(m2)
+    rho0 = W.random_density(b2.dim, seed=5)
+    w2 = np.random.default_rng(3).uniform(-1, 1, b2.dim)
+    _, _, _, gga2 = oracle.adjoint_gradients(m2, w2, n_steps=30, rho0=rho0, basis=b2, scheme="strang")
+
+    def loss2(jumps):
+        rho = oracle.evolve(dict(m2, jumps=jumps), n_steps=30, rho0=rho0, basis=b2, return_records=False,
+                            scheme="strang")
+        return float(np.sum(w2 * np.real(np.diag(rho))))
+
+    for j in range(len(m2["jumps"])):
+        fd = stencil(lambda d: loss2([(k, s, g + (d if q == j else 0.0)) for q, (k, s, g) in enumerate(m2["jumps"])]))
+        assert abs(gga2[j] - fd) <= 1e-6 * abs(fd) + 1e-10, (j, gga2[j], fd)
+
+
+def test_strang_adjoint_without_jumps_equals_the_lie_adjoint():
+    """With no jumps both steps are U rho U^+, so the two adjoints coincide."""
+    m = W.jch_two_cavities(gamma=0.0)
+    m["jumps"] = []
+    b = oracle.enumerate_basis(m)
+    w = np.random.default_rng(8).uniform(0, 1, b.dim)
+    a = oracle.adjoint_gradients(m, w, n_steps=50, basis=b)
+    s = oracle.adjoint_gradients(m, w, n_steps=50, basis=b, scheme="strang")
+    assert abs(a[0] - s[0]) < 1e-15
+    for x, y in zip(a[1:3], s[1:3]):
+        assert np.abs(x - y).max() < 1e-15
