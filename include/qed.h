@@ -163,7 +163,7 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every);
  * qed_evolve and qed_evolve_batched use from now on; the Strang scheme runs four Lindblad
  * stages per step instead of one.  EINVAL for an unknown scheme; ENOMEM if the FP64 path's
  * stage buffer cannot be allocated.  Synchronises the device.  qed_adjoint differentiates
- * the Lie step only (EUNSUPPORTED otherwise). */
+ * the Strang step on the FP64 path (EUNSUPPORTED in split precision). */
 qed_status qed_set_scheme(qed_model *m, int32_t scheme);
 
 /* ---------------------------------------------------------------- hot path */
@@ -200,8 +200,11 @@ qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_off
  * order of the spec (each may be NULL only if its count is 0).  FP64 models use FP64
  * kernels throughout; split-precision models run the forward steps, the co-state steps
  * (as a backward model with U^+ and the outgoing jump lists) and the products
- * rho_n lambda_n in split precision, accumulating M in FP64.  EUNSUPPORTED under
- * QED_SCHEME_STRANG.  Allocates its work space per call; synchronises `stream`.
+ * rho_n lambda_n in split precision, accumulating M in FP64.  Under QED_SCHEME_STRANG
+ * (FP64 models only; EUNSUPPORTED in split precision) the adjoint of the symmetric step:
+ * kappa_n = E^+(lambda_{n+1}), mu_n = U^+ kappa_n U, lambda_n = E^+(mu_n) with E the
+ * midpoint half step, M = sum_n E(rho_n) U^+ kappa_n, and the rate gradients of both half
+ * steps.  Allocates its work space per call; synchronises `stream`.
  */
 qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t checkpoint_every,
                        const double *obs_diag, double *loss, double *grad_g, double *grad_zeta,

@@ -596,6 +596,108 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
     return QED_OK;
 }
 
+// The adjoint of the Strang step on the FP64 path.  Forward: X_n = E(rho_n),
+// V_n = U X_n U^+, rho_{n+1} = E(V_n), E the explicit-midpoint half step (tau = dt/2) of the
+// Lindblad term.  Backward: kappa_n = E^+(lambda_{n+1}), mu_n = U^+ kappa_n U,
+// lambda_n = E^+(mu_n), with E^+(Lam) = Lam + tau L^+(T), T = Lam + tau/2 L^+(Lam) (L^+ from
+// the outgoing jump lists); M = sum_n X_n U^+ kappa_n for the Frechet contraction; every rate
+// gradient gets tau tr(T D_j(Y)) + tau^2/2 tr(Lam D_j(L Y)) from each half step (Lam, Y) =
+// (lambda_{n+1}, V_n) and (mu_n, rho_n).
+qed_status adjoint_strang_f64(qed_model *m, const void *rho0, int64_t N, int64_t k, const double *obs_diag,
+                              double *loss, double *grad_g, double *grad_zeta, double *grad_gamma, cudaStream_t s) {
+    AdjointState &a = *m->adj;
+    const int64_t D = m->D;
+    const size_t DD = (size_t)(D * D);
+    k = std::min<int64_t>(k, std::max<int64_t>(N, 1));
+    const int64_t n_ck = N > 0 ? (N - 1) / k + 1 : 0;
+    const double tau = 0.5 * m->dt;
+    Buffers B;
+    double2 *ck = nullptr, *seg_rho = nullptr, *seg_x = nullptr, *seg_v = nullptr, *rho = nullptr, *lam = nullptr,
+            *kap = nullptr, *mu = nullptr, *T1 = nullptr, *Ly = nullptr, *Z = nullptr, *Macc = nullptr, *T = nullptr;
+    double *r = nullptr;
+    ADJ_TRY(B.get(&ck, DD * (size_t)std::max<int64_t>(n_ck, 1)));
+    ADJ_TRY(B.get(&seg_rho, DD * (size_t)k));
+    ADJ_TRY(B.get(&seg_x, DD * (size_t)k));
+    ADJ_TRY(B.get(&seg_v, DD * (size_t)k));
+    for (double2 **q : {&rho, &lam, &kap, &mu, &T1, &Ly, &Z, &Macc, &T}) ADJ_TRY(B.get(q, DD));
+    ADJ_TRY(B.get(&r, (size_t)D));
+    QED_CUDA_TRY(cudaMemsetAsync(Z, 0, DD * 16, s));
+    // forward L stages (incoming lists) and backward L^+ stages (outgoing lists)
+    auto fwd = [&](const double2 *X, const double2 *Bv, double2 *out, double t) {
+        lindblad_axpy_f64(s, D, X, Bv, out, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, t);
+    };
+    auto bwd = [&](const double2 *X, const double2 *Bv, double2 *out, double t) {
+        lindblad_axpy_f64(s, D, X, Bv, out, m->anti, a.out_ptr, a.out_jump, a.out_dst, a.out_coef, t);
+    };
+    // one forward step from rho (in place), keeping X and V
+    auto step = [&](double2 *x, double2 *v) {
+        fwd(rho, rho, T1, 0.5 * tau);
+        fwd(T1, rho, x, tau);
+        zgemm(s, D, D, D, 1.0, m->U, D, x, D, false, 0.0, T, D);
+        zgemm(s, D, D, D, 1.0, T, D, m->U, D, true, 0.0, v, D);
+        fwd(v, v, T1, 0.5 * tau);
+        fwd(T1, v, rho, tau);
+    };
+    auto rate = [&](const double2 *Lam, const double2 *Y, double scale) {
+        rowdot_kernel<<<blocks_for(D, 8), 256, 0, s>>>(D, Lam, Y, r);
+        gamma_grad_kernel<<<a.n_jumps, 256, 0, s>>>(D, a.je_ptr, a.je_src, a.je_dst, a.je_coef, Lam, Y, r, scale,
+                                                    grad_gamma);
+        count_launches(2);
+    };
+    const int64_t last0 = (n_ck - 1) * k;  // the last segment is stored by the forward pass
+    QED_CUDA_TRY(cudaMemcpyAsync(rho, rho0, DD * 16, cudaMemcpyDeviceToDevice, s));
+    for (int64_t n = 0; n < N; ++n) {
+        if (n % k == 0 && n < last0)
+            QED_CUDA_TRY(cudaMemcpyAsync(ck + (size_t)(n / k) * DD, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
+        const bool keep = n >= last0;
+        const size_t o = keep ? (size_t)(n - last0) * DD : 0;
+        if (keep) QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + o, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
+        step(keep ? seg_x + o : Ly, keep ? seg_v + o : mu);
+    }
+    loss_kernel<<<1, 256, 0, s>>>(D, rho, obs_diag, loss);
+    set_diag_kernel<<<blocks_for((int64_t)DD, 256), 256, 0, s>>>(D, obs_diag, lam);
+    count_launches(2);
+    QED_CUDA_TRY(cudaMemsetAsync(Macc, 0, DD * 16, s));
+    if (a.n_jumps > 0) QED_CUDA_TRY(cudaMemsetAsync(grad_gamma, 0, (size_t)a.n_jumps * 8, s));
+    for (int64_t c = n_ck - 1; c >= 0; --c) {
+        const int64_t s0 = c * k, s1 = std::min(N, s0 + k);
+        if (c < n_ck - 1) {  // recompute the segment, keeping rho_n, X_n and V_n
+            QED_CUDA_TRY(cudaMemcpyAsync(rho, ck + (size_t)c * DD, DD * 16, cudaMemcpyDeviceToDevice, s));
+            for (int64_t n = s0; n < s1; ++n) {
+                const size_t o = (size_t)(n - s0) * DD;
+                QED_CUDA_TRY(cudaMemcpyAsync(seg_rho + o, rho, DD * 16, cudaMemcpyDeviceToDevice, s));
+                step(seg_x + o, seg_v + o);
+            }
+        }
+        for (int64_t n = s1 - 1; n >= s0; --n) {
+            const size_t o = (size_t)(n - s0) * DD;
+            const double2 *rn = seg_rho + o, *xn = seg_x + o, *vn = seg_v + o;
+            // kappa_n = E^+(lambda_{n+1}), its stage T1
+            bwd(lam, lam, T1, 0.5 * tau);
+            bwd(T1, lam, kap, tau);
+            if (a.n_jumps > 0) {
+                fwd(vn, Z, Ly, 1.0);  // L(V_n)
+                rate(T1, vn, tau);
+                rate(lam, Ly, 0.5 * tau * tau);
+            }
+            // M += X_n U^+ kappa_n;  mu_n = U^+ kappa_n U
+            zgemm(s, D, D, D, 1.0, xn, D, m->U, D, true, 0.0, T, D);
+            zgemm(s, D, D, D, 1.0, T, D, kap, D, false, 1.0, Macc, D);
+            zgemm(s, D, D, D, 1.0, kap, D, m->U, D, false, 0.0, T, D);
+            zgemm_ex(s, D, D, D, 1.0, m->U, D, true, T, D, false, 0.0, mu, D);
+            // lambda_n = E^+(mu_n), its stage T1
+            bwd(mu, mu, T1, 0.5 * tau);
+            bwd(T1, mu, lam, tau);
+            if (a.n_jumps > 0) {
+                fwd(rn, Z, Ly, 1.0);  // L(rho_n)
+                rate(T1, rn, tau);
+                rate(mu, Ly, 0.5 * tau * tau);
+            }
+        }
+    }
+    return frechet_gradients(m, B, Macc, grad_g, grad_zeta, s);
+}
+
 }  // namespace
 
 void adjoint_release(qed_model *m) {
@@ -625,8 +727,8 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: n_steps >= 0 and checkpoint_every > 0 required");
         return QED_EINVAL;
     }
-    if (m->scheme != QED_SCHEME_LIE) {
-        set_error("qed_adjoint: only the Lie step is differentiated");
+    if (m->scheme != QED_SCHEME_LIE && m->prec != QED_FP64) {
+        set_error("qed_adjoint: the Strang step is differentiated on the FP64 path only");
         return QED_EUNSUPPORTED;
     }
     ADJ_TRY(setup(m));
@@ -638,6 +740,9 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
     cudaStream_t s = (cudaStream_t)stream;
     if (m->prec != QED_FP64)
         return adjoint_split(m, rho0, n_steps, checkpoint_every, obs_diag, loss, grad_g, grad_zeta, grad_gamma, s);
+    if (m->scheme == QED_SCHEME_STRANG)
+        return adjoint_strang_f64(m, rho0, n_steps, checkpoint_every, obs_diag, loss, grad_g, grad_zeta, grad_gamma,
+                                  s);
     const int64_t D = m->D;
     const size_t DD = (size_t)(D * D);
     const int64_t N = n_steps, k = std::min<int64_t>(checkpoint_every, std::max<int64_t>(n_steps, 1));

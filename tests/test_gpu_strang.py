@@ -120,13 +120,48 @@ def test_batched_strang_matches_oracle():
 
 def test_scheme_errors():
     m = W.jch_two_cavities()
-    gm = qed.Model(m, precision="fp64", scheme="strang")
+    gm = qed.Model(m, precision="split_fp16x2", scheme="strang")
     b = oracle.enumerate_basis(m)
     w = np.zeros(b.dim)
-    with pytest.raises(qed.QedError):  # the adjoint differentiates the Lie step only
+    with pytest.raises(qed.QedError):  # the Strang step is differentiated on the FP64 path only
         gm.adjoint(_cuda(oracle.initial_density(m, b)), 10, _cuda(w), checkpoint_every=5)
     a = qed.Model(m, precision="split_fp16x2")
     c = qed.Model(m, precision="split_fp16x2", scheme="strang")
     rhos = [_cuda(oracle.initial_density(m, b)) for _ in range(2)]
     with pytest.raises(qed.QedError):  # one scheme per batch
         qed.evolve_batched([a, c], rhos, 5)
+
+
+def _close(a, b, rtol):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.abs(a - b).max() <= rtol * max(np.abs(b).max(), 1e-30)
+
+
+@pytest.mark.parametrize("k", [7, 100])
+def test_fp64_strang_adjoint_matches_oracle(k):
+    """The adjoint of the Strang step (FP64 path) against the oracle's, on a 3 x 3 lattice
+    (leaks) with ragged checkpoint segments and with every state kept, and on a two-cavity
+    model with photon loss, atom decay and dephasing from a random mixed state."""
+    m = W.lattice(3, 3, seed=4, gamma=0.02, dt=0.1, n_steps=60, start=(0, 0))
+    b = oracle.enumerate_basis(m)
+    w = oracle.loss_diag(m, b, photons=[0], atoms=[0])
+    ref = oracle.adjoint_gradients(m, w, basis=b, scheme="strang")
+    gm = qed.Model(m, precision="fp64", scheme="strang")
+    loss, gg, gz, gj = gm.adjoint(_cuda(oracle.initial_density(m, b)), 60, _cuda(w), checkpoint_every=k)
+    assert abs(float(loss) - ref[0]) <= 1e-12
+    for x, y in zip((gg, gz, gj), ref[1:]):
+        assert _close(x.cpu().numpy(), y, 1e-9)
+
+    m2 = W.hb_shaped(gamma=0.02, gamma_pos=0.03)
+    m2.update(n_cavities=2, atoms_per_cavity=[1, 1], n_max=[2, 2], g=[0.013, 0.017], bonds=[(0, 1)],
+              zeta=[0.006], dt=0.1)
+    m2["jumps"] = list(m2["jumps"]) + [(1, 0, 0.01)]
+    b2 = oracle.enumerate_basis(m2)
+    rho0 = W.random_density(b2.dim, seed=5)
+    w2 = np.random.default_rng(3).uniform(-1, 1, b2.dim)
+    ref2 = oracle.adjoint_gradients(m2, w2, n_steps=30, rho0=rho0, basis=b2, scheme="strang")
+    g2 = qed.Model(m2, precision="fp64", scheme="strang")
+    loss2, gg2, gz2, gj2 = g2.adjoint(_cuda(rho0), 30, _cuda(w2), checkpoint_every=k)
+    assert abs(float(loss2) - ref2[0]) <= 1e-12
+    for x, y in zip((gg2, gz2, gj2), ref2[1:]):
+        assert _close(x.cpu().numpy(), y, 1e-9)
