@@ -805,10 +805,12 @@ void launch_lindblad(const Batch &b, int xsel, int bsel, int osel, float f, int 
     count_launches(1);
 }
 // The two stages of one explicit-midpoint half step of the Lindblad flow (step dt/2):
-// Y = X + (dt/4) L(X), then rho = X + (dt/2) L(Y) with its planes.
-void launch_half_lindblad(const Batch &b, int xsel, cudaStream_t s) {
+// Y = X + (dt/4) L(X), then rho = X + (dt/2) L(Y), with its planes when the next kernel is
+// GEMM1 (the leading half step; the trailing one is always followed by the next leading
+// half step, a renormalisation or the end of the run, none of which read the planes).
+void launch_half_lindblad(const Batch &b, int xsel, int planes, cudaStream_t s) {
     launch_lindblad(b, xsel, xsel, 2, 0.25f, 0, s);
-    launch_lindblad(b, 2, xsel, 0, 0.5f, 1, s);
+    launch_lindblad(b, 2, xsel, 0, 0.5f, planes, s);
 }
 
 }  // namespace
@@ -935,13 +937,13 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
 }
 
 void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
-    if (b.scheme == QED_SCHEME_STRANG) launch_half_lindblad(b, 0, s);  // rho <- E(dt/2) rho
+    if (b.scheme == QED_SCHEME_STRANG) launch_half_lindblad(b, 0, 1, s);  // rho <- E(dt/2) rho
     launch_gemm1(b, err, s);  // unsplit: its epilogue writes W, W^T and the W planes
     if (b.w_reduce) launch_w_reduce(b, s);
     launch_gemm2(b, err, s);
     launch_form(b, s);
     if (b.scheme == QED_SCHEME_STRANG)
-        launch_half_lindblad(b, 1, s);  // rho <- E(dt/2) V
+        launch_half_lindblad(b, 1, 0, s);  // rho <- E(dt/2) V
     else
         launch_dissipate(b, s);
 }
@@ -971,7 +973,7 @@ int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
         cudaEventRecord(m->ev[e++], s);
         launch_lindblad(b, 1, 1, 2, 0.25f, 0, s);
         cudaEventRecord(m->ev[e++], s);
-        launch_lindblad(b, 2, 1, 0, 0.5f, 1, s);
+        launch_lindblad(b, 2, 1, 0, 0.5f, 0, s);
         cudaEventRecord(m->ev[e++], s);
         label = "lindblad_a,lindblad_b,gemm1_tc,w_reduce,gemm2_tc,form_v,lindblad_c,lindblad_d";
         return 8;
