@@ -270,8 +270,11 @@ __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
 // writes W, its transpose (through a shared-memory tile so both stores coalesce) and its
 // FP16 hi/lo planes as GEMM2's A operand, row k = [W_re[k, :] | W_im[k, :]].  One block
 // per 32 x 32 tile of one instance.
-__global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restrict__ tiles,
-                                                       const InstDesc *__restrict__ descs) {
+// Threads of w_reduce in y: each covers 32 / kWY rows of its 32 x 32 tile.
+constexpr int kWY = 16;
+
+__global__ void __launch_bounds__(32 * kWY) w_reduce_kernel(const TileItem *__restrict__ tiles,
+                                                            const InstDesc *__restrict__ descs) {
     __shared__ float tre[32][33], tim[32][33];
     // the work item and the descriptor are written once at set-up: read them while the
     // previous kernel finishes
@@ -280,12 +283,12 @@ __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restric
     pdl_wait();
     pdl_trigger();
     const int64_t Dp = a.Dp;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x kWY
     const int64_t k0 = (int64_t)it.by * 32, l0 = (int64_t)it.bx * 32;
     const int64_t stride = 2 * Dp * Dp, plane = Dp * 2 * Dp;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t k = k0 + ty + 8 * q, l = l0 + tx;
+    for (int q = 0; q < 32 / kWY; ++q) {
+        const int64_t k = k0 + ty + kWY * q, l = l0 + tx;
         float re = 0.f, im = 0.f;
         for (int s = 0; s < a.splits1; ++s) {
             re += a.part[s * stride + k * Dp + l];
@@ -295,8 +298,8 @@ __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restric
         im *= a.inv_w;
         a.w32[k * Dp + l] = re;
         a.w32[Dp * Dp + k * Dp + l] = im;
-        tre[ty + 8 * q][tx] = re;
-        tim[ty + 8 * q][tx] = im;
+        tre[ty + kWY * q][tx] = re;
+        tim[ty + kWY * q][tx] = im;
         const float xr = re * a.s_w, xi = im * a.s_w;
         __half h = __float2half_rn(xr);
         a.w_pl[k * 2 * Dp + l] = h;
@@ -307,10 +310,10 @@ __global__ void __launch_bounds__(256) w_reduce_kernel(const TileItem *__restric
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t l = l0 + ty + 8 * q, k = k0 + tx;
-        a.wt32[l * Dp + k] = tre[tx][ty + 8 * q];
-        a.wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + 8 * q];
+    for (int q = 0; q < 32 / kWY; ++q) {
+        const int64_t l = l0 + ty + kWY * q, k = k0 + tx;
+        a.wt32[l * Dp + k] = tre[tx][ty + kWY * q];
+        a.wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + kWY * q];
     }
 }
 
@@ -788,7 +791,7 @@ void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
     tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, err, s);
 }
 void launch_w_reduce(const Batch &b, cudaStream_t s) {
-    launch_pdl(w_reduce_kernel, dim3(b.n_wtiles), dim3(32, 8), 0, s, b.wtiles, b.desc);
+    launch_pdl(w_reduce_kernel, dim3(b.n_wtiles), dim3(32, kWY), 0, s, b.wtiles, b.desc);
     count_launches(1);
 }
 void launch_form(const Batch &b, cudaStream_t s) {
