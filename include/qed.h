@@ -45,7 +45,7 @@ typedef enum {
     QED_ECUDA = 3,         /* a CUDA runtime/driver call failed                */
     QED_ETIMEOUT = 4,      /* a bounded device wait ran out                    */
     QED_ENUMERIC = 5,      /* non-finite values or a singular Pade denominator */
-    QED_EUNSUPPORTED = 6   /* valid request this build does not implement      */
+    QED_EUNSUPPORTED = 6   /* valid request the library does not implement     */
 } qed_status;
 
 typedef enum {

@@ -357,7 +357,7 @@ qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_st
     *out = nullptr;
     if (!(dt > 0.0) || !std::isfinite(dt)) return einval("dt must be finite and > 0");
     if (prec != QED_FP64 && prec != QED_SPLIT_FP16x2) {
-        set_error("precision not implemented in this build");
+        set_error("precision not implemented by this library");
         return QED_EUNSUPPORTED;
     }
     std::unique_ptr<qed_model, void (*)(qed_model *)> m(new qed_model(), release);
