@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="split_fp16x2")
+    p.add_argument("--autotune", action="store_true", help="time the tile choices before the run (qed_autotune)")
     p.add_argument("--scheme", default="lie", choices=["lie", "strang"],
                    help="time-stepping scheme (the adjoint workload differentiates the Lie step only)")
     p.add_argument("--qme-steps", type=int, default=None)
@@ -212,6 +213,7 @@ def run_ours(args):
     qme_steps = args.qme_steps or model["n_steps"]
     r = model["record_every"]
     gm = qed.Model(model, precision=args.precision, scheme=args.scheme)
+    tuned = gm.autotune(20) if args.autotune else None
     D = gm.dim
     obs = list(range(D))
     i0 = gm.initial_index()
@@ -318,7 +320,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f16x2->f32 (split), f64 master" if args.precision != "fp64" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "dim": D, "qme_steps_per_step": qme_steps, "dt": model["dt"],
-                   "record_every": r, "precision": args.precision, "scheme": args.scheme,
+                   "record_every": r, "precision": args.precision, "scheme": args.scheme, "autotuned": tuned,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) between timed iterations; working set < L2 within a run"},
         "complex_tflops": complex_tflops(D, value / world) * world,

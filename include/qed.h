@@ -166,6 +166,16 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every);
  * the Strang step on the FP64 path (EUNSUPPORTED in split precision). */
 qed_status qed_set_scheme(qed_model *m, int32_t scheme);
 
+/* Tile autotuner for a split-precision model stepped on its own (qed_evolve): times
+ * `steps` whole steps for each candidate tile width (128 or 256 columns) and split-K
+ * factor (1, 2, 4) of the step's two tensor-core products, GEMM1's candidates first, then
+ * GEMM2's with the best GEMM1, and keeps the fastest.  (The batched path plans its own
+ * grouped launches.)  Writes a description of the choice into `choice` (size choice_cap;
+ * may be NULL).  Uses the model's internal state as scratch (the next qed_evolve imports
+ * rho again) and drops the captured step graphs; synchronises the device.  FP64 models
+ * have nothing to tune (OK).  EINVAL for steps <= 0. */
+qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choice_cap, qed_stream stream);
+
 /* ---------------------------------------------------------------- hot path */
 
 /*

@@ -77,6 +77,7 @@ def lib():
         "qed_n_observables": [vp, _c_int32_p],
         "qed_set_renorm_every": [vp, i32],
         "qed_set_scheme": [vp, i32],
+        "qed_autotune": [vp, i32, ctypes.c_char_p, i32, vp],
         "qed_evolve": [vp, vp, i64, i64, i32, i32, _c_int32_p, vp, vp],
         "qed_observables": [vp, vp, i32, _c_int32_p, vp, vp],
         "qed_sync_status": [vp, vp],
@@ -313,6 +314,13 @@ class Model:
 
     def set_renorm_every(self, every):
         _check(lib().qed_set_renorm_every(self._h, int(every)), "qed_set_renorm_every")
+
+    def autotune(self, steps=20, stream=None):
+        """Times the step's tile widths and split-K factors (qed_autotune) and keeps the
+        fastest; returns the description of the choice."""
+        buf = ctypes.create_string_buffer(256)
+        _check(lib().qed_autotune(self._h, int(steps), buf, 256, _stream_handle(stream)), "qed_autotune")
+        return buf.value.decode()
 
     def set_scheme(self, scheme):
         """'lie' (first order) or 'strang' (second order: half Lindblad steps by the explicit

@@ -417,6 +417,27 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every) {
     return QED_OK;
 }
 
+qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choice_cap, qed_stream stream) {
+    if (!m || steps <= 0) return einval("qed_autotune: NULL model or steps <= 0");
+    std::string c = "FP64 model: no tile choices";
+    if (m->prec != QED_FP64) {
+        // the captured step graphs hold the old step tables
+        QED_CUDA_TRY(cudaDeviceSynchronize());
+        for (auto &g : m->graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        QED_TRY(split_autotune(m, (cudaStream_t)stream, steps, c));
+        QED_TRY(qed_sync_status(m, stream));
+    }
+    if (choice && choice_cap > 0) {
+        std::strncpy(choice, c.c_str(), (size_t)choice_cap - 1);
+        choice[choice_cap - 1] = 0;
+    }
+    return QED_OK;
+}
+
 qed_status qed_set_scheme(qed_model *m, int32_t scheme) {
     if (!m || (scheme != QED_SCHEME_LIE && scheme != QED_SCHEME_STRANG)) return einval("bad scheme");
     if (scheme == m->scheme) return QED_OK;

@@ -108,6 +108,7 @@ struct SplitState {
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
     float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
     int4 *in_tab = nullptr;                  // padded incoming table (rows with <= kInMax entries)
+    int partial_slices = 0;                  // split-K slices `partial` has room for
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
 };
 
@@ -851,8 +852,8 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
             return QED_ECUDA;
         if (!tc_gemm_plan(S.g2, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), 3, seg2, S.num_sms))
             return QED_ECUDA;
-        const size_t partial = (size_t)std::max(S.g1.splits, S.g2.splits) * 2 * Dp * Dp;
-        SPLIT_TRY(alloc(&S.partial, partial));
+        S.partial_slices = std::max(S.g1.splits, S.g2.splits);
+        SPLIT_TRY(alloc(&S.partial, (size_t)S.partial_slices * 2 * Dp * Dp));
 
         // per-row phases P_k as double-floats
         std::vector<double2> ph((size_t)D);
@@ -952,6 +953,84 @@ void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
 }
 
 void split_step(qed_model *m, cudaStream_t s) { batch_step(m->sp->self, m->err, s); }
+
+// Chooses the tile width and split-K factor of each of the model's two products by timing
+// whole steps (so the slice reductions the split products need are part of the cost):
+// GEMM1's candidates with GEMM2 as planned, then GEMM2's with the best GEMM1.  Candidates:
+// 128- and 256-wide tiles, 1, 2 or 4 slices.  Overwrites the internal state (qed_evolve
+// imports rho again) and replaces the step tables; the caller drops its captured graphs.
+qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &choice) {
+    SplitState &S = *m->sp;
+    const int64_t Dp = S.Dp;
+    if (S.partial_slices < kTcMaxAutoSplits) {
+        QED_CUDA_TRY(cudaStreamSynchronize(s));
+        cudaFree(S.partial);
+        S.partial = nullptr;
+        SPLIT_TRY(alloc(&S.partial, (size_t)kTcMaxAutoSplits * 2 * Dp * Dp));
+        S.partial_slices = kTcMaxAutoSplits;
+    }
+    qed_model *self[1] = {m};
+    const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
+    const int seg2[6] = {0, 0, 1, 0, 0, 1};
+    auto candidates = [&](int which, std::vector<TcGemm> &out) -> qed_status {
+        for (int bn : {128, 256})
+            for (int sp : {1, 2, 4}) {
+                TcGemm g;
+                const bool ok = which == 1 ? tc_gemm_plan(g, S.a1, 3, S.rho_pl, 2, (int)(2 * Dp), (int)Dp,
+                                                          (int)(2 * Dp), 4, seg1, S.num_sms, sp, bn)
+                                           : tc_gemm_plan(g, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp),
+                                                          (int)(2 * Dp), 3, seg2, S.num_sms, sp, bn);
+                if (!ok) return QED_ECUDA;
+                bool seen = false;
+                for (const auto &h : out) seen = seen || (h.bn == g.bn && h.splits == g.splits);
+                if (!seen) out.push_back(g);
+            }
+        return QED_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QED_CUDA_TRY(cudaEventCreate(&e0));
+    QED_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_steps = [&](float &ms) -> qed_status {
+        SPLIT_TRY(build_batch(S.self, self, 1, true));
+        for (int i = 0; i < 2; ++i) batch_step(S.self, m->err, s);
+        QED_CUDA_TRY(cudaEventRecord(e0, s));
+        for (int i = 0; i < steps; ++i) batch_step(S.self, m->err, s);
+        QED_CUDA_TRY(cudaEventRecord(e1, s));
+        QED_CUDA_TRY(cudaEventSynchronize(e1));
+        QED_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        return QED_OK;
+    };
+    qed_status st = QED_OK;
+    float best = 0.f;
+    TcGemm g1 = S.g1, g2 = S.g2;
+    std::vector<TcGemm> c1, c2;
+    if ((st = candidates(1, c1)) == QED_OK && (st = candidates(2, c2)) == QED_OK && (st = time_steps(best)) == QED_OK) {
+        for (const auto &g : c1) {
+            S.g1 = g;
+            S.g2 = g2;
+            float t = 0.f;
+            if ((st = time_steps(t)) != QED_OK) break;
+            if (t < best) best = t, g1 = g;
+        }
+        for (size_t i = 0; st == QED_OK && i < c2.size(); ++i) {
+            S.g1 = g1;
+            S.g2 = c2[i];
+            float t = 0.f;
+            if ((st = time_steps(t)) != QED_OK) break;
+            if (t < best) best = t, g2 = c2[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    S.g1 = g1;
+    S.g2 = g2;
+    if (st != QED_OK) return st;
+    SPLIT_TRY(build_batch(S.self, self, 1, true));
+    choice = "gemm1 " + std::to_string(g1.bn) + "-wide x" + std::to_string(g1.splits) + " slices, gemm2 " +
+             std::to_string(g2.bn) + "-wide x" + std::to_string(g2.splits) + " slices, " +
+             std::to_string(1e3 * best / steps) + " us per step";
+    return QED_OK;
+}
 
 void split_set_scheme(qed_model *m, int scheme) {
     if (m->sp) m->sp->self.scheme = scheme;

@@ -14,6 +14,9 @@ qed_status split_prepare(qed_model *m, cudaStream_t s);                 // Delta
 qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s);  // caller rho -> internal state
 void split_step(qed_model *m, cudaStream_t s);
 void split_set_scheme(qed_model *m, int scheme);  // QED_SCHEME_LIE or QED_SCHEME_STRANG
+// Times whole steps over the tile widths and split-K factors of both products and keeps
+// the fastest; `choice` describes it.
+qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &choice);
 void split_renorm(qed_model *m, cudaStream_t s);
 void split_observables(qed_model *m, const int32_t *ids, int32_t n_obs, double *out, cudaStream_t s);
 void split_end(qed_model *m, double2 *rho, cudaStream_t s);              // internal state -> caller rho

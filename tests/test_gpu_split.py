@@ -216,3 +216,22 @@ def test_split_two_bond_size_d4096_against_fp64_gpu():
     # (~1e-13 per step); the last symmetrisation was 80 steps before the end
     assert np.abs(r - r.conj().T).max() <= 1e-10
     assert np.real(np.diag(r)).min() >= -1e-6
+
+
+@pytest.mark.parametrize("make,steps", [(lambda: W.jch_two_cavities(), 400), (lambda: W.hb_shaped(), 200)])
+def test_autotuned_plan_keeps_parity(make, steps):
+    """qed_autotune times the tile widths and split-K factors of both products and keeps the
+    fastest; whatever it picks, the step still matches the oracle."""
+    m = make()
+    b = oracle.enumerate_basis(m)
+    gm = qed.Model(m, precision="split_fp16x2")
+    choice = gm.autotune(10)
+    print(f"{m['name']}: {choice}")
+    assert choice.startswith("gemm1 ")
+    obs = list(range(b.dim))
+    rho_ref, rec_ref = oracle.evolve(m, n_steps=steps, record_every=50, basis=b, obs_ids=obs)
+    rho = _cuda(oracle.initial_density(m, b))
+    rec = gm.evolve(rho, steps, record_every=50, obs_ids=obs)
+    gm.sync()
+    assert np.abs(rho.cpu().numpy() - rho_ref).max() <= RHO_TOL
+    assert np.abs(rec.cpu().numpy() - rec_ref).max() <= POP_TOL
