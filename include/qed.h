@@ -129,6 +129,14 @@ qed_status qed_spec_hamiltonian(const qed_spec *spec, double *H, int64_t capacit
 /* Dense projected A_j (not scaled by gamma), host complex128 [dim x dim]. */
 qed_status qed_spec_jump(const qed_spec *spec, int32_t j, double *A, int64_t capacity);
 
+/* The operators of the model restricted to the basis states keep[0..n-1] (increasing
+ * indices into the spec's basis), as qed_select_states builds them (Sec. 3.2): j = -1 gives
+ * P H P, j >= 0 gives P A_j P (not scaled by gamma), host complex128 [n x n]; d (host FP64
+ * [n], or NULL) receives d_k = sum_j gamma_j (P A_j^+ P A_j P)_kk.  EINVAL for an empty or
+ * unsorted list or a small buffer. */
+qed_status qed_spec_restricted(const qed_spec *spec, const int64_t *keep, int64_t n, int32_t j, double *out,
+                               int64_t capacity, double *d);
+
 /* ---------------------------------------------------------------- model lifetime */
 
 /* Build basis, H, jump tables and observables on the host, upload them, and compute

@@ -69,6 +69,8 @@ def lib():
         "qed_spec_basis": [ctypes.POINTER(QedSpec), _c_int32_p, i64],
         "qed_spec_hamiltonian": [ctypes.POINTER(QedSpec), _c_double_p, i64],
         "qed_spec_jump": [ctypes.POINTER(QedSpec), i32, _c_double_p, i64],
+        "qed_spec_restricted": [ctypes.POINTER(QedSpec), ctypes.POINTER(i64), i64, i32, _c_double_p, i64,
+                                _c_double_p],
         "qed_build": [ctypes.POINTER(QedSpec), dbl, i32, vp, ctypes.POINTER(vp)],
         "qed_free": [vp],
         "qed_dim": [vp, ctypes.POINTER(i64)],
@@ -171,6 +173,20 @@ def spec_jump(model, j):
     out = np.zeros((D, D), dtype=np.complex128)
     _check(lib().qed_spec_jump(ctypes.byref(s), j, out.ctypes.data_as(_c_double_p), D * D), "qed_spec_jump")
     return out
+
+
+def spec_restricted(model, keep, j=-1):
+    """(P H P if j < 0 else P A_j P, d) on the basis states `keep` (host query of the
+    operators qed_select_states builds)."""
+    s, _k = make_spec(model)
+    keep = np.ascontiguousarray(keep, dtype=np.int64)
+    n = len(keep)
+    out = np.zeros((n, n), dtype=np.complex128)
+    d = np.zeros(n, dtype=np.float64)
+    _check(lib().qed_spec_restricted(ctypes.byref(s), keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n,
+                                     int(j), out.ctypes.data_as(_c_double_p), n * n, d.ctypes.data_as(_c_double_p)),
+           "qed_spec_restricted")
+    return out, d
 
 
 def digit_positions(model):

@@ -352,6 +352,29 @@ qed_status qed_spec_jump(const qed_spec *spec, int32_t j, double *A, int64_t cap
     return QED_OK;
 }
 
+qed_status qed_spec_restricted(const qed_spec *spec, const int64_t *keep, int64_t n, int32_t j, double *out,
+                               int64_t capacity, double *d) {
+    if (!keep || n <= 0 || !out) return einval("qed_spec_restricted: bad argument");
+    HostModel hm, sub;
+    std::string err;
+    qed_status st = build_host_model(spec, hm, err, true);
+    if (st != QED_OK) { set_error(err); return st; }
+    if (!restrict_host_model(hm, std::vector<int64_t>(keep, keep + n), sub, err)) return einval(err);
+    if (capacity < n * n) return einval("qed_spec_restricted: buffer too small");
+    if (j >= (int32_t)sub.gamma.size()) return einval("jump index out of range");
+    if (j < 0) {
+        std::vector<cplx> Hd;
+        dense_hamiltonian(sub, Hd);
+        std::memcpy(out, Hd.data(), Hd.size() * sizeof(cplx));
+    } else {
+        std::memset(out, 0, (size_t)(n * n) * 16);
+        for (const auto &e : sub.jumps)
+            if (e.jump == j) out[2 * (e.dst * n + e.src)] += e.coef;
+    }
+    if (d) std::copy(sub.anti_diag.begin(), sub.anti_diag.end(), d);
+    return QED_OK;
+}
+
 qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_stream stream, qed_model **out) {
     if (!out) return einval("out is NULL");
     *out = nullptr;

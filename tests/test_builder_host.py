@@ -112,3 +112,30 @@ def test_empty_sector_is_rejected():
     m["excitation_cap"] = 9
     with pytest.raises(qed.QedError):
         qed.spec_dim(m)
+
+
+@pytest.mark.parametrize("name", ["hb_shaped_d512", "lattice_6x5"])
+def test_restricted_operators_match_oracle_projection(name):
+    """The model on a subset of the basis (what qed_select_states builds after deleting
+    states): P H P and P A_j P equal the oracle's operators restricted to the kept rows and
+    columns, and d_k = sum_j gamma_j (A_j^+ A_j)_kk of the projected jumps."""
+    m = W.hb_shaped() if name == "hb_shaped_d512" else W.lattice(6, 5, seed=7, gamma=5e-3)
+    b = oracle.enumerate_basis(m)
+    keep = np.sort(np.random.default_rng(1).choice(b.dim, size=b.dim // 3, replace=False))
+    H, d = qed.spec_restricted(m, keep, -1)
+    assert np.abs(H - oracle.hamiltonian(m, b)[np.ix_(keep, keep)]).max() <= 1e-15
+    d_ref = np.zeros(len(keep))
+    for j, (gamma, A) in enumerate(oracle.jump_operators(m, b)):
+        Ak = A.toarray()[np.ix_(keep, keep)]
+        Aj, _ = qed.spec_restricted(m, keep, j)
+        assert np.abs(Aj - Ak).max() == 0.0
+        d_ref += gamma * np.real(np.diag(Ak.conj().T @ Ak))
+    assert np.abs(d - d_ref).max() <= 1e-15
+
+
+def test_restricted_operators_reject_bad_lists():
+    m = W.jch_two_cavities()
+    with pytest.raises(qed.QedError):
+        qed.spec_restricted(m, [3, 1], -1)      # not increasing
+    with pytest.raises(qed.QedError):
+        qed.spec_restricted(m, [0, 99], -1)     # outside the basis
