@@ -139,3 +139,12 @@ def test_restricted_operators_reject_bad_lists():
         qed.spec_restricted(m, [3, 1], -1)      # not increasing
     with pytest.raises(qed.QedError):
         qed.spec_restricted(m, [0, 99], -1)     # outside the basis
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libqed.so every call raises instead of computing elsewhere."""
+    import paper_2403_07042_gb300 as pkg
+    monkeypatch.setattr(pkg, "_lib", None)
+    monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "libqed.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.spec_dim(W.jch_two_cavities())
