@@ -174,7 +174,8 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every);
  * the Strang step on the FP64 path (EUNSUPPORTED in split precision). */
 qed_status qed_set_scheme(qed_model *m, int32_t scheme);
 
-/* Tile autotuner for a split-precision model stepped on its own (qed_evolve): times
+/* Tile autotuner (the paper has no counterpart: it concerns only how this library maps the
+ * step's products onto the GPU) for a split-precision model stepped on its own: times
  * `steps` whole steps for each candidate tile width (128 or 256 columns) and split-K
  * factor (1, 2, 4) of the step's two tensor-core products, GEMM1's candidates first, then
  * GEMM2's with the best GEMM1, and keeps the fastest.  (The batched path plans its own
