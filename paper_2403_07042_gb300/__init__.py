@@ -215,8 +215,7 @@ def tc_gemm(a_planes, b_planes, segments=((0, 0), (0, 1), (1, 0)), splits=1, str
     A_p B_q^T, the FP16 tensor-core product of the split-precision step; a_planes
     [planes, M, K] and b_planes [planes, N, K] are CUDA float16."""
     import torch
-    M, K = a_planes.shape[1], a_planes.shape[2]
-    N = b_planes.shape[1]
+    M, N, K = _check_planes(a_planes, b_planes)
     seg = _arr([x for pq in segments for x in pq], np.int32)
     out = torch.empty((splits, M, N), dtype=torch.float32, device=a_planes.device)
     _check(lib().qed_tc_gemm(ctypes.c_void_p(a_planes.data_ptr()), a_planes.shape[0],
@@ -231,17 +230,36 @@ def tc_gemm_static(a_planes, b_planes, segments=((0, 0), (0, 1), (1, 0)), splits
     allocation inside the library: its split-K partials use the library's static scratch
     (splits * M * N <= 4 Mi floats).  `out` may be a caller-owned CUDA float32 tensor."""
     import torch
-    M, K = a_planes.shape[1], a_planes.shape[2]
-    N = b_planes.shape[1]
+    M, N, K = _check_planes(a_planes, b_planes)
     seg = _arr([x for pq in segments for x in pq], np.int32)
     if out is None:
         out = torch.empty((M, N), dtype=torch.float32, device=a_planes.device)
+    if (not isinstance(out, torch.Tensor) or out.dtype != torch.float32 or out.device != a_planes.device
+            or tuple(out.shape) != (M, N) or not out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous float32 ({M}, {N}) tensor on {a_planes.device}")
     _check(lib().qed_tc_gemm_static(ctypes.c_void_p(a_planes.data_ptr()), a_planes.shape[0],
                                     ctypes.c_void_p(b_planes.data_ptr()), b_planes.shape[0], M, N, K,
                                     len(segments), seg.ctypes.data_as(_c_int32_p), splits,
                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
            "qed_tc_gemm_static")
     return out
+
+
+def _check_planes(a_planes, b_planes):
+    """(M, N, K) of the FP16 operand stacks a_planes [planes, M, K] and b_planes [planes, N, K];
+    both must be contiguous CUDA float16 tensors on one device with the same K (the library
+    reads them through tensor maps encoded from these sizes)."""
+    import torch
+    for name, t in (("a_planes", a_planes), ("b_planes", b_planes)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float16 or not t.is_cuda or t.dim() != 3:
+            raise TypeError(f"{name} must be a 3-d CUDA float16 tensor [planes, rows, K]")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if a_planes.device != b_planes.device:
+        raise ValueError("a_planes and b_planes must be on one device")
+    if a_planes.shape[2] != b_planes.shape[2]:
+        raise ValueError(f"a_planes and b_planes must share K (got {a_planes.shape[2]} and {b_planes.shape[2]})")
+    return a_planes.shape[1], b_planes.shape[1], a_planes.shape[2]
 
 
 def _stream_handle(stream):

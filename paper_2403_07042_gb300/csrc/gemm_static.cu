@@ -4,6 +4,7 @@
 // output.  For callers that must not allocate device memory (for example code running
 // inside another framework's memory pool, or a process whose allocations are fixed up
 // front): it calls no cudaMalloc, cudaFree or allocating library routine.
+#include <mutex>
 #include <string>
 
 #include "gemm_tc.h"
@@ -29,6 +30,7 @@ struct StaticPtrs {
 };
 
 StaticPtrs g_ptrs[kMaxDevices];
+std::mutex g_ptrs_mutex;  // first calls on a device from several host threads
 
 // out[i] = sum over s of part[s * MN + i], in a fixed order
 __global__ void sum_partials_kernel(int64_t MN, int splits, const float *part, float *out) {
@@ -48,16 +50,21 @@ qed_status static_ptrs(StaticPtrs *&p) {
         set_error("qed_tc_gemm_static: no usable current device");
         return QED_ECUDA;
     }
+    std::lock_guard<std::mutex> lock(g_ptrs_mutex);
     p = &g_ptrs[dev];
     if (p->ready) return QED_OK;
-    cudaError_t e1 = cudaGetSymbolAddress((void **)&p->scratch, g_static_scratch);
-    cudaError_t e2 = cudaGetSymbolAddress((void **)&p->err, g_static_err);
+    float *scratch = nullptr;
+    uint32_t *err = nullptr;
+    cudaError_t e1 = cudaGetSymbolAddress((void **)&scratch, g_static_scratch);
+    cudaError_t e2 = cudaGetSymbolAddress((void **)&err, g_static_err);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaGetLastError();
         set_error(std::string("qed_tc_gemm_static: cudaGetSymbolAddress failed: ") +
                   cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
         return QED_ECUDA;
     }
+    p->scratch = scratch;
+    p->err = err;
     p->ready = true;
     return QED_OK;
 }
@@ -98,10 +105,22 @@ extern "C" qed_status qed_tc_gemm_static(const void *a_planes, int32_t planes_a,
         set_error("qed_tc_gemm_static: cudaMemsetAsync failed");
         return QED_ECUDA;
     }
-    tc_gemm_launch(g, sp->scratch, sp->err, s);
+    // the partial sums are only read if the product's own launch was accepted (otherwise the
+    // scratch still holds the previous call's partials)
+    cudaError_t le = tc_gemm_launch(g, sp->scratch, sp->err, s);
+    if (le != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("qed_tc_gemm_static: tensor-core launch failed: ") + cudaGetErrorString(le));
+        return QED_ECUDA;
+    }
     const int64_t MN = (int64_t)M * N;
     sum_partials_kernel<<<(unsigned)((MN + 255) / 256), 256, 0, s>>>(MN, splits, sp->scratch, out);
     count_launches(1);
+    le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        set_error(std::string("qed_tc_gemm_static: summation launch failed: ") + cudaGetErrorString(le));
+        return QED_ECUDA;
+    }
     uint32_t h = 0;
     cudaMemcpyAsync(&h, sp->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);

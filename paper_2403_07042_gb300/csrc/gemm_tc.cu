@@ -483,7 +483,7 @@ bool tc_gemm_prepare_grouped() {
     return true;
 }
 
-void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) {
+cudaError_t tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) {
     Params p;
     p.M = g.M;
     p.N = g.N;
@@ -503,10 +503,8 @@ void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s) 
     p.err = err;
     dim3 grid((g.N + g.bn - 1) / g.bn, g.M / kTcBM, g.splits);
     count_launches(1);
-    if (g.bn == 128)
-        launch_pdl(tc_gemm_kernel<128>, grid, dim3(128), tc_gemm_smem_bytes(128), s, g.a, g.b, p);
-    else
-        launch_pdl(tc_gemm_kernel<256>, grid, dim3(128), tc_gemm_smem_bytes(256), s, g.a, g.b, p);
+    if (g.bn == 128) return launch_pdl(tc_gemm_kernel<128>, grid, dim3(128), tc_gemm_smem_bytes(128), s, g.a, g.b, p);
+    return launch_pdl(tc_gemm_kernel<256>, grid, dim3(128), tc_gemm_smem_bytes(256), s, g.a, g.b, p);
 }
 
 }  // namespace qed
@@ -534,8 +532,15 @@ extern "C" qed_status qed_tc_gemm(const void *a_planes, int32_t planes_a, const 
         return QED_ENOMEM;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    cudaMemsetAsync(err, 0, 4, s);
-    tc_gemm_launch(g, out, err, s);
+    cudaError_t le = cudaMemsetAsync(err, 0, 4, s);
+    if (le == cudaSuccess) le = tc_gemm_launch(g, out, err, s);
+    if (le != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaFree(err);
+        set_error(std::string("qed_tc_gemm: launch failed: ") + cudaGetErrorString(le));
+        return QED_ECUDA;
+    }
     uint32_t h = 0;
     cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);

@@ -43,8 +43,9 @@ __host__ __device__ constexpr int tc_stages(int bn) { return bn == 128 ? 6 : 4; 
 bool tc_gemm_plan(TcGemm &g, const void *a_planes, int planes_a, const void *b_planes, int planes_b, int M, int N,
                   int K, int nseg, const int *seg_pairs, int num_sms, int force_splits = 0, int force_bn = 0);
 
-// Launch on `s`; `err` receives kErrTimeout if a bounded wait ran out.
-void tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s);
+// Launch on `s`; `err` receives kErrTimeout if a bounded wait ran out.  Returns the
+// status of the launch itself (a launch-configuration error is reported here, not later).
+cudaError_t tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStream_t s);
 
 // Epilogues: kEpiPlain stores the FP32 tile into its split-K slice; kEpiW (for unsplit
 // products) treats the output as GEMM1's [W_re; W_im]

@@ -51,6 +51,42 @@ def test_static_scratch_gemm_matches_tc_gemm_twice():
         assert np.all(np.abs(got - exact) <= bound)
 
 
+def test_static_scratch_allocates_nothing_and_leaves_no_stale_partials():
+    """After a first call (which looks up the array's device address), further calls leave
+    the device's free memory unchanged; a same-shape call with new inputs returns the new
+    product, not partial sums left in the shared array by the previous call."""
+    rng = np.random.default_rng(7)
+    M, N, K, splits, seg = 256, 256, 256, 4, ((0, 0), (0, 1), (1, 0))
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    A0 = torch.from_numpy(_pieces(rng, M, K, 2)).cuda()
+    B0 = torch.from_numpy(_pieces(rng, N, K, 2)).cuda()
+    qed.tc_gemm_static(A0, B0, segments=seg, splits=splits, out=out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        qed.tc_gemm_static(A0, B0, segments=seg, splits=splits, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    A1 = torch.from_numpy(_pieces(rng, M, K, 2)).cuda()
+    B1 = torch.from_numpy(_pieces(rng, N, K, 2)).cuda()
+    got = qed.tc_gemm_static(A1, B1, segments=seg, splits=splits, out=out).double().cpu().numpy()
+    Af, Bf = A1.double().cpu().numpy(), B1.double().cpu().numpy()
+    exact = sum(Af[p] @ Bf[q].T for p, q in seg)
+    bound = len(seg) * K * 2.0 ** -23 * (np.abs(Af).sum(0) @ np.abs(Bf).sum(0).T)
+    assert np.all(np.abs(got - exact) <= bound)
+
+
+def test_static_scratch_rejects_bad_out():
+    A = torch.zeros((2, 128, 64), dtype=torch.float16, device="cuda")
+    B = torch.zeros((2, 128, 64), dtype=torch.float16, device="cuda")
+    with pytest.raises(ValueError):
+        qed.tc_gemm_static(A, B, out=torch.empty((64, 128), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        qed.tc_gemm_static(A, B, out=torch.empty((128, 128), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        qed.tc_gemm_static(A, torch.zeros((2, 128, 128), dtype=torch.float16, device="cuda"))
+
+
 def test_static_scratch_rejects_oversize():
     A = torch.zeros((2, 2048, 64), dtype=torch.float16, device="cuda")
     B = torch.zeros((2, 2048, 64), dtype=torch.float16, device="cuda")
