@@ -197,6 +197,14 @@ qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choic
  * with (step_offset + i) % record_every == 0; records may be NULL when n_obs == 0.
  * n_rec = number of such i.  Asynchronous on `stream`: device-side errors (non-finite
  * trace at a renormalisation) surface through qed_sync_status.
+ *
+ * Split precision (QED_SPLIT_FP16x2) accepts only a density matrix: rho Hermitian and of
+ * unit trace (|rho_mn - conj(rho_nm)| <= 1e-8 and |tr rho - 1| <= 1e-6).  Its first product
+ * reads the row-major rho as rho^T = conj(rho), the second forms the Hermitian X = W Delta^+,
+ * the FP16 scale assumes |rho_mn| <= 1 and the renormalisation divides by tr rho; any other
+ * input would give a silently different answer.  A device check at the start of the call
+ * flags a violation, which qed_sync_status returns as EINVAL (the evolved rho is then
+ * meaningless).  The FP64 path takes any complex D x D matrix.
  */
 qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_offset,
                       int32_t record_every, int32_t n_obs, const int32_t *obs_ids,
@@ -223,7 +231,8 @@ qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_off
  * (FP64 models only; EUNSUPPORTED in split precision) the adjoint of the symmetric step:
  * kappa_n = E^+(lambda_{n+1}), mu_n = U^+ kappa_n U, lambda_n = E^+(mu_n) with E the
  * midpoint half step, M = sum_n E(rho_n) U^+ kappa_n, and the rate gradients of both half
- * steps.  Allocates its work space per call; synchronises `stream`.
+ * steps.  In split precision rho0 must be Hermitian with unit trace (EINVAL otherwise, as
+ * in qed_evolve).  Allocates its work space per call; synchronises `stream`.
  */
 qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t checkpoint_every,
                        const double *obs_diag, double *loss, double *grad_g, double *grad_zeta,
@@ -239,7 +248,10 @@ qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t 
  * once.  records (host array of n device pointers, or NULL): records[i] (device FP64, or
  * NULL) receives the populations rho_kk of instance i, row-major [n_rec x D_i], at steps
  * 0, r, 2r, ... <= n_steps (r = record_every).  Each model's renormalisation setting
- * applies.  Synchronises `stream` before returning (it frees the batch's tables).
+ * applies.  Split precision requires each rho to be Hermitian with unit trace (as in
+ * qed_evolve); a violation, like any device-side error of an instance, is returned by this
+ * call (EINVAL, ETIMEOUT, ENUMERIC) after the final synchronisation.  Synchronises `stream`
+ * before returning (it frees the batch's tables).
  */
 qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos, int64_t n_steps,
                               int32_t record_every, double *const *records, qed_stream stream);

@@ -530,6 +530,7 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
     ADJ_TRY(B.get(&r, (size_t)D));
     // forward with checkpoints of the double-float state
     const int64_t last0 = (n_ck - 1) * k;  // the last segment is stored by the forward pass
+    split_check_density(m, (const double2 *)rho0, s);
     ADJ_TRY(split_begin(m, (const double2 *)rho0, s));
     for (int64_t n = 0; n < N; ++n) {
         if (n % k == 0 && n < last0)
@@ -576,7 +577,7 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
             a_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, rn, (float)s_a, a.a_pl);
             b_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, split_vbuf(t), (float)s_b, a.b_pl);
             count_launches(2);
-            tc_gemm_launch(a.g, a.c_slices, m->err, s);
+            QED_CUDA_TRY(tc_gemm_launch(a.g, a.c_slices, m->err, s));
             acc_kernel<<<rows, 256, 0, s>>>(D, Dp, a.g.splits, a.c_slices, o_scale / (s_a * s_b), Nacc);
             count_launches(1);
         }
@@ -592,6 +593,11 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
         QED_CUDA_TRY(cudaMemset(t->err, 0, 4));
         set_error("qed_adjoint: a bounded device wait ran out");
         return QED_ETIMEOUT;
+    }
+    if (flags[0] & kErrNotDensity) {
+        QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+        set_error("qed_adjoint: split precision needs a Hermitian rho0 of unit trace");
+        return QED_EINVAL;
     }
     return QED_OK;
 }

@@ -490,6 +490,7 @@ qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_o
     const int64_t D = m->D;
     const bool split = m->prec != QED_FP64;
     if (split) {
+        split_check_density(m, rho, s);
         QED_TRY(split_begin(m, rho, s));
     } else {
         if (!m->rho_int) QED_TRY(dev_alloc(&m->rho_int, (size_t)(D * D)));
@@ -550,7 +551,10 @@ qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos
         }
         return QED_OK;
     }
-    for (int32_t i = 0; i < n; ++i) QED_TRY(split_begin(ms[i], (const double2 *)rhos[i], s));
+    for (int32_t i = 0; i < n; ++i) {
+        split_check_density(ms[i], (const double2 *)rhos[i], s);
+        QED_TRY(split_begin(ms[i], (const double2 *)rhos[i], s));
+    }
     Batch *b = nullptr;
     QED_TRY(split_batch_create(ms, n, &b));
     // the step loop as graphs of 1 and kGraphSteps grouped steps
@@ -616,6 +620,9 @@ qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos
     split_batch_destroy(b);
     if (st != QED_OK) return st;
     QED_CUDA_TRY(cudaGetLastError());
+    // the call has synchronised: report device-side errors (a rejected rho, a bounded wait
+    // that ran out) of every instance now
+    for (int32_t i = 0; i < n; ++i) QED_TRY(qed_sync_status(ms[i], stream));
     return QED_OK;
 }
 
@@ -642,6 +649,11 @@ qed_status qed_sync_status(qed_model *m, qed_stream stream) {
     if (e & kErrTimeout) { set_error("a bounded device wait ran out"); return QED_ETIMEOUT; }
     if (e & kErrNonFinite) { set_error("non-finite or non-positive trace at renormalisation"); return QED_ENUMERIC; }
     if (e & kErrSingular) { set_error("singular matrix"); return QED_ENUMERIC; }
+    if (e & kErrNotDensity) {
+        set_error("split precision needs a Hermitian rho of unit trace (|rho_mn - conj(rho_nm)| <= 1e-8, "
+                  "|tr rho - 1| <= 1e-6); that rho was evolved regardless and the result is not meaningful");
+        return QED_EINVAL;
+    }
     return QED_OK;
 }
 

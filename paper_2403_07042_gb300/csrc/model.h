@@ -30,7 +30,12 @@ enum : uint32_t {
     kErrNonFinite = 1u,
     kErrSingular = 2u,
     kErrTimeout = 4u,
+    kErrNotDensity = 8u,   // split precision given a rho that is not Hermitian with unit trace
 };
+
+// Tolerances of that check (absolute): max |rho_mn - conj(rho_nm)| and |tr rho - 1|.
+constexpr double kDensityHermTol = 1e-8;
+constexpr double kDensityTraceTol = 1e-6;
 
 // State of the split-precision (increment form) path; defined in split.cu.
 struct SplitState;

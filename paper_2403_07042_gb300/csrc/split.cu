@@ -260,6 +260,32 @@ __global__ void planes_from_state_kernel(int64_t D, int64_t Dp, const float4 *st
     pl[plane + m * 2 * Dp + Dp + n] = l;
 }
 
+// The split path's precondition on the caller's rho: Hermitian (its GEMM1 operand is the
+// row-major rho read as rho^T = conj(rho), and X = W Delta^+ is formed as a Hermitian
+// matrix) and of unit trace (the FP16 scale assumes |rho_mn| <= 1 and the renormalisation
+// divides by the trace).  One thread per pair m <= n; block 0 also sums the diagonal.
+__global__ void __launch_bounds__(256) check_density_kernel(int64_t D, const double2 *rho, uint32_t *err) {
+    __shared__ double part[256];
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int64_t n = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t m = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    if (m < D && n < D && n >= m) {
+        const double2 a = rho[m * D + n], b = rho[n * D + m];
+        const double dr = fabs(a.x - b.x), di = fabs(a.y + b.y);
+        if (!(dr <= kDensityHermTol) || !(di <= kDensityHermTol)) atomicOr(err, kErrNotDensity);
+    }
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+    double s = 0.0;
+    for (int64_t k = t; k < D; k += 256) s += rho[k * D + k].x;
+    part[t] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) part[t] += part[t + h];
+        __syncthreads();
+    }
+    if (t == 0 && !(fabs(part[0] - 1.0) <= kDensityTraceTol)) atomicOr(err, kErrNotDensity);
+}
+
 __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= D * D) return;
@@ -938,6 +964,12 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
     count_launches(1);
     QED_CUDA_TRY(cudaGetLastError());
     return QED_OK;
+}
+
+void split_check_density(qed_model *m, const double2 *rho, cudaStream_t s) {
+    dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
+    check_density_kernel<<<grid, dim3(32, 8), 0, s>>>(m->D, rho, m->err);
+    count_launches(1);
 }
 
 void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {

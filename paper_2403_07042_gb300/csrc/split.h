@@ -12,6 +12,9 @@ namespace qed {
 
 qed_status split_prepare(qed_model *m, cudaStream_t s);                 // Delta planes, buffers, TMA maps
 qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s);  // caller rho -> internal state
+// Sets kErrNotDensity in m->err unless rho (caller layout) is Hermitian with unit trace
+// within kDensityHermTol / kDensityTraceTol: the increment form relies on both.
+void split_check_density(qed_model *m, const double2 *rho, cudaStream_t s);
 void split_step(qed_model *m, cudaStream_t s);
 void split_set_scheme(qed_model *m, int scheme);  // QED_SCHEME_LIE or QED_SCHEME_STRANG
 // Times whole steps over the tile widths and split-K factors of both products and keeps
