@@ -2,6 +2,8 @@
 
 Calls only the FP64 oracle (and the seeded workload module).  Usage:
     python tests/golden/make_golden.py hb_shaped_d512
+    python tests/golden/make_golden.py jch2_d36
+    python tests/golden/make_golden.py batched_chains_d53_1008
     python tests/golden/make_golden.py adjoint_lattice_24x24_d1153
 """
 import os
@@ -16,18 +18,46 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle  # noqa: E402
 import qed_workloads as W  # noqa: E402
 
-SAMPLED_ROWS = [0, 1, 2, 3, 64, 100, 255, 256, 300, 511]
-
-
 def hb_shaped_d512():
     """The hydrogen-bond-shaped workload (dim 512), 10000 steps of dt 0.05: populations
-    every 100 steps and ten full rows of the final density matrix."""
+    every 100 steps and the whole final density matrix (512 x 512 complex128)."""
     m = W.hb_shaped()
     b = oracle.enumerate_basis(m)
     t0 = time.time()
     rho, rec = oracle.evolve(m, basis=b, obs_ids=list(range(b.dim)))
-    np.savez_compressed(os.path.join(HERE, "hb_shaped_d512_oracle.npz"), records=rec,
-                        rho_rows=np.array(SAMPLED_ROWS), rho_sample=rho[SAMPLED_ROWS],
+    np.savez_compressed(os.path.join(HERE, "hb_shaped_d512_oracle.npz"), records=rec, rho=rho,
+                        trace=np.trace(rho).real, seconds=time.time() - t0)
+
+
+def batched_chains_d53_1008():
+    """The first 16 instances of the batched-chains workload (seed 0: the same instances the
+    512-instance bench run starts with; dims 53..1008), 1000 steps of dt 0.1 each:
+    populations every 100 steps and eight rows of each final density matrix (evenly spaced,
+    first and last included).  Instance i's arrays are stored under the suffix _i."""
+    specs = W.batched_chains(16, seed=0)
+    out = {}
+    t0 = time.time()
+    for i, m in enumerate(specs):
+        b = oracle.enumerate_basis(m)
+        rho, rec = oracle.evolve(m, basis=b, obs_ids=list(range(b.dim)))
+        rows = np.unique(np.linspace(0, b.dim - 1, 8).round().astype(np.int64))
+        out[f"records_{i}"] = rec
+        out[f"rows_{i}"] = rows
+        out[f"rho_rows_{i}"] = rho[rows]
+        out[f"trace_{i}"] = np.trace(rho).real
+        print(f"instance {i}: dim {b.dim}, {time.time() - t0:.0f} s", flush=True)
+    np.savez_compressed(os.path.join(HERE, "batched_chains_d53_1008_oracle.npz"), n=len(specs),
+                        seconds=time.time() - t0, **out)
+
+
+def jch2_d36():
+    """Two coupled JC cavities (dim 36), 20000 steps of dt 0.1: populations every 100 steps
+    and the whole final density matrix."""
+    m = W.jch_two_cavities()
+    b = oracle.enumerate_basis(m)
+    t0 = time.time()
+    rho, rec = oracle.evolve(m, basis=b, obs_ids=list(range(b.dim)))
+    np.savez_compressed(os.path.join(HERE, "jch2_d36_oracle.npz"), records=rec, rho=rho,
                         trace=np.trace(rho).real, seconds=time.time() - t0)
 
 

@@ -1,5 +1,8 @@
 """Batched evolution of uneven instances (qed_evolve_batched): every instance against the
-FP64 oracle, and against the same model evolved on its own."""
+FP64 oracle (at small sizes run here, at the workload's own scale from stored oracle
+trajectories), and against the same model evolved on its own."""
+import os
+
 import numpy as np
 import pytest
 
@@ -7,6 +10,7 @@ import oracle
 import qed_workloads as W
 
 pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 torch = pytest.importorskip("torch")
 qed = pytest.importorskip("paper_2403_07042_gb300")
@@ -32,19 +36,28 @@ def _setup(specs, precision):
     return models, rhos
 
 
+def _oracle_U(m, b):
+    return oracle.propagator(oracle.hamiltonian(m, b), m["dt"])
+
+
 @pytest.mark.parametrize("precision,tol_rho,tol_pop", [("split_fp16x2", 1e-5, 1e-6), ("fp64", 1e-12, 1e-12)])
 def test_batched_instances_match_oracle(precision, tol_rho, tol_pop):
-    """16 seeded chains (dims 32..256, several tiles, ragged), 300 steps, records every 50."""
+    """16 seeded chains (dims 32..256, several tiles, ragged), 300 steps, records every 50.
+    The oracle steps with its own eigendecomposition U; the FP64 instances are given that U
+    (qed_set_U), so the comparison isolates the step, and the GPU's own Pade U is checked
+    against it separately."""
     specs = W.batched_chains(16, seed=3, dim_lo=32, dim_hi=256, n_steps=300, record_every=50)
     models, rhos = _setup(specs, precision)
+    bases = [oracle.enumerate_basis(m) for m in specs]
+    Us = [_oracle_U(m, b) for m, b in zip(specs, bases)]
+    if precision == "fp64":
+        for gm, U in zip(models, Us):
+            assert np.abs(gm.get_U().cpu().numpy() - U).max() <= 1e-14
+            gm.set_U(torch.from_numpy(U).cuda())
     recs = qed.evolve_batched(models, rhos, 300, record_every=50)
     torch.cuda.synchronize()
     worst = 0.0
-    for m, gm, r, rec in zip(specs, models, rhos, recs):
-        b = oracle.enumerate_basis(m)
-        U = None
-        if precision == "fp64":
-            U = gm.get_U().cpu().numpy()
+    for m, b, U, r, rec in zip(specs, bases, Us, rhos, recs):
         rho_ref, rec_ref = oracle.evolve(m, n_steps=300, record_every=50, basis=b, U=U,
                                          obs_ids=list(range(b.dim)))
         err = np.abs(r.cpu().numpy() - rho_ref).max()
@@ -52,6 +65,39 @@ def test_batched_instances_match_oracle(precision, tol_rho, tol_pop):
         worst = max(worst, err)
         assert err <= tol_rho and perr <= tol_pop, (m["name"], err, perr)
     print(f"batched {precision}: worst max|drho| over 16 instances = {worst:.2e}")
+
+
+@pytest.mark.parametrize("precision,tol_rho,tol_pop", [("split_fp16x2", 1e-5, 1e-6), ("fp64", 1e-12, 1e-12)])
+def test_batched_chains_full_size_against_stored_oracle(precision, tol_rho, tol_pop):
+    """The batched-chains workload at its own scale: the first 16 of its 512 seeded instances
+    (dims 53..1008, the instances the bench's run starts with), 1000 steps of dt 0.1,
+    populations every 100 steps, against the oracle trajectories stored by
+    tests/golden/make_golden.py (every population record and eight rows of each final rho).
+    Split precision runs exactly as benchmarked (the GPU's own U); the FP64 instances are
+    given the oracle's eigendecomposition U (qed_set_U) so the 1e-12 bar applies to the step,
+    and each GPU Pade U is checked against that U to 1e-14."""
+    g = np.load(os.path.join(GOLDEN, "batched_chains_d53_1008_oracle.npz"))
+    specs = W.batched_chains(int(g["n"]), seed=0)
+    assert specs[0]["n_steps"] == 1000 and specs[0]["record_every"] == 100
+    models, rhos = _setup(specs, precision)
+    dims = [gm.dim for gm in models]
+    assert min(dims) == 53 and max(dims) == 1008
+    if precision == "fp64":
+        for m, gm in zip(specs, models):
+            U = _oracle_U(m, oracle.enumerate_basis(m))
+            assert np.abs(gm.get_U().cpu().numpy() - U).max() <= 1e-14
+            gm.set_U(torch.from_numpy(U).cuda())
+    recs = qed.evolve_batched(models, rhos, 1000, record_every=100)
+    torch.cuda.synchronize()
+    worst, worst_p = 0.0, 0.0
+    for i, (r, rec) in enumerate(zip(rhos, recs)):
+        rows = g[f"rows_{i}"]
+        err = np.abs(r.cpu().numpy()[rows] - g[f"rho_rows_{i}"]).max()
+        perr = np.abs(rec.cpu().numpy() - g[f"records_{i}"]).max()
+        worst, worst_p = max(worst, err), max(worst_p, perr)
+        assert err <= tol_rho and perr <= tol_pop, (i, dims[i], err, perr)
+    print(f"batched chains d53..1008 {precision}, 1000 steps: max|drho| (sampled rows) = {worst:.2e}, "
+          f"max|dpop| = {worst_p:.2e}")
 
 
 def test_batched_equals_single_model_runs():
@@ -75,3 +121,9 @@ def test_batched_argument_errors():
     m64, r64 = _setup(specs[:1], "fp64")
     with pytest.raises(qed.QedError):
         qed.evolve_batched([models[0], m64[0]], [rhos[0], r64[0]], 5)
+    # split precision: a rho that is not a density matrix is reported by the call itself
+    bad = rhos[1].clone()
+    bad[0, 1] += 1e-3
+    with pytest.raises(qed.QedError) as ei:
+        qed.evolve_batched(models, [rhos[0], bad], 5)
+    assert ei.value.status == qed.QED_EINVAL

@@ -148,18 +148,16 @@ def test_split_jch2_full_length():
 
 def test_split_hb_shaped_full_length_against_stored_oracle():
     """The dim-512 workload at full length (10000 steps), in the configuration the bench
-    times, against the stored oracle trajectory (populations every 100 steps, ten rows of
-    the final rho), written by tests/golden/make_golden.py."""
-    path = os.path.join(GOLDEN, "hb_shaped_d512_oracle.npz")
-    if not os.path.exists(path):
-        pytest.skip("stored oracle trajectory not generated")
-    g = np.load(path)
+    times, against the stored oracle trajectory (populations every 100 steps and every
+    element of the final 512 x 512 rho), written by tests/golden/make_golden.py."""
+    g = np.load(os.path.join(GOLDEN, "hb_shaped_d512_oracle.npz"))
     m = W.hb_shaped()
     rho, rec = _evolve(m, m["n_steps"], "split_fp16x2", record_every=m["record_every"],
                        obs=list(range(512)))
-    err = np.abs(rho[g["rho_rows"]] - g["rho_sample"]).max()
+    assert g["rho"].shape == rho.shape == (512, 512)
+    err = np.abs(rho - g["rho"]).max()
     perr = np.abs(rec - g["records"]).max()
-    print(f"hb_shaped split 10000 steps: max|drho| (sampled rows)={err:.2e} max|dpop|={perr:.2e}")
+    print(f"hb_shaped split 10000 steps: max|drho| (all 262144 elements)={err:.2e} max|dpop|={perr:.2e}")
     assert perr <= POP_TOL and err <= RHO_TOL
     assert abs(np.trace(rho).real - 1.0) <= 1e-7
     assert np.abs(rho - rho.conj().T).max() <= 1e-12
@@ -177,6 +175,50 @@ def test_split_invariants_and_renormalisation():
     assert abs(np.trace(r).real - 1.0) <= 1e-12
     assert np.abs(r - r.conj().T).max() <= 1e-15
     assert np.linalg.eigvalsh(r).min() >= -1e-6
+
+
+@pytest.mark.parametrize("defect", ["not_hermitian", "trace_half", "trace_two"])
+def test_split_rejects_non_density_input(defect):
+    """The split path needs a Hermitian, unit-trace rho (its first product reads rho^T as
+    conj(rho), the second forms a Hermitian X, the renormalisation divides by the trace):
+    other inputs are reported as EINVAL by qed_sync_status.  The FP64 path takes them and
+    matches the oracle's step of the same matrix."""
+    m = W.jch_two_cavities()
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=11)
+    if defect == "not_hermitian":
+        rho0 = rho0.copy()
+        rho0[3, 7] += 1e-3j
+    else:
+        rho0 = rho0 * (0.5 if defect == "trace_half" else 2.0)
+    gs = qed.Model(m, precision="split_fp16x2")
+    rho = _cuda(rho0)
+    gs.evolve(rho, 10)
+    with pytest.raises(qed.QedError) as ei:
+        gs.sync()
+    assert ei.value.status == qed.QED_EINVAL
+    # the model stays usable: a proper density matrix afterwards passes
+    ok = _cuda(W.random_density(b.dim, seed=12))
+    gs.evolve(ok, 10)
+    gs.sync()
+    # the FP64 path accepts any matrix and follows the oracle's map of it
+    U = oracle.propagator(oracle.hamiltonian(m, b), m["dt"])
+    rho_ref = oracle.evolve(m, rho0=rho0, n_steps=10, U=U, basis=b, return_records=False)
+    r64, _ = _evolve(m, 10, "fp64", rho0=rho0, U=U)
+    assert np.abs(r64 - rho_ref).max() <= 1e-12
+
+
+def test_split_accepts_its_own_output():
+    """A state the split path returned mid-way between renormalisations (here 150 steps
+    with the default interval of 100) passes the density check of the next call."""
+    m = W.hb_shaped()
+    b = oracle.enumerate_basis(m)
+    gs = qed.Model(m, precision="split_fp16x2")
+    rho = _cuda(W.random_density(b.dim, seed=4, rank=3))
+    gs.evolve(rho, 150)
+    gs.sync()
+    gs.evolve(rho, 20)
+    gs.sync()
 
 
 def test_split_nonfinite_is_reported():
