@@ -30,26 +30,21 @@
 #include "kernels.h"
 #include "pdl.h"
 #include "split.h"
+#include "df.h"
 
 namespace qed {
 
 // Device-side description of one instance (one model) for the grouped kernels.
 struct InstDesc {
     int64_t D, Dp;
-    int splits1, splits2;   // split-K slices of GEMM1 / GEMM2
-    float inv_w;            // 1 / (s_Delta s_rho): GEMM1 sums -> W
-    float s_w;              // scale of the W planes
-    float inv_x;            // 1 / (s_W s_Delta): GEMM2 sums -> X
     float s_rho;            // scale of the rho planes
-    float *part;            // split-K partial sums (GEMM1, then GEMM2)
-    float *w32, *wt32;
     float4 *rho, *V, *Y;    // state, V = U rho U^+, stage buffer of the Strang step
     const float4 *phase;
     const float2 *damp;
     const int32_t *in_ptr, *in_jump, *in_src;
     const float2 *coef;
     const int4 *in_tab;     // [D][kInMax] {jump, src, coef hi, coef lo} or null (use the lists)
-    __half *rho_pl, *w_pl;
+    __half *rho_pl;
 };
 
 // Rows with at most kInMax incoming jump entries use a padded table (one vector load per
@@ -58,10 +53,8 @@ constexpr int kInMax = 4;
 constexpr int kNoJump = 0x7fffffff;
 // Pairs of incoming lists longer than this in total are merged by the whole warp.
 constexpr int kLongMerge = 32;
-// Split-K slices the element-wise kernels sum (the plan's cap).
-constexpr int kMaxSlices = kTcMaxAutoSplits;
 
-// 32 x 32 tiles of W (w_reduce) or 32 x 8 element blocks (form_v, dissipate) of one instance
+// 32 x 8 element blocks (the Lindblad kernels) of one instance
 struct TileItem {
     int inst, bx, by, pad;
 };
@@ -74,14 +67,19 @@ struct Batch {
     CUtensorMap *maps = nullptr;  // [4 n]: A1, B1, A2, B2 of each instance
     GemmItem *items1 = nullptr, *items2 = nullptr;
     int n_items1 = 0, n_items2 = 0;
-    TileItem *wtiles = nullptr, *etiles = nullptr;
-    int n_wtiles = 0, n_etiles = 0;
-    int cs1 = 1, cs2 = 1;  // split-K slices of GEMM1 / GEMM2
-    bool w_reduce = false;  // GEMM1 split: a separate pass sums its slices into W
+    TileItem *etiles = nullptr;
+    int n_etiles = 0;
+    int cs1 = 1, cs2 = 1;  // split-K slices of GEMM1 / GEMM2 = CTAs per cluster
     int scheme = QED_SCHEME_LIE;
-    int bn1 = 256, bn2 = 256;  // tile widths (one per grouped launch)
+    int bn1 = 256, bn2 = 128;  // tile widths (one per grouped launch; GEMM2's is 128)
+    // one model on its own: its products launch with their tensor maps and jobs as kernel
+    // parameters (tc_gemm_single_launch) instead of through the tables above
+    bool single = false;
+    int64_t D = 0;
+    TcGemm g1, g2;
+    GemmJob j1, j2;
     void release() {
-        void *ptrs[] = {desc, jobs1, jobs2, maps, items1, items2, wtiles, etiles};
+        void *ptrs[] = {desc, jobs1, jobs2, maps, items1, items2, etiles};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         *this = Batch();
@@ -95,87 +93,23 @@ struct SplitState {
     TcGemm g1, g2;
     // constant operands, FP16 [3 (hi, mid, lo)][2Dp][2Dp]
     __half *a1 = nullptr;     // [[Dre, Dim], [Dim, -Dre]]   (GEMM1 A)
-    __half *b2 = nullptr;     // [[Dre, Dim], [-Dim, Dre]]   (GEMM2 B)
+    __half *b2 = nullptr;     // [[Dre, Dim], [-Dim, Dre]]   (GEMM2 B), rows in [re | im] groups of 64
     // dynamic operands, FP16 [2 (hi, lo)][Dp][2Dp]
     __half *rho_pl = nullptr; // rows l: [rho_re | rho_im]
     __half *w_pl = nullptr;   // rows k: [W_re | W_im]
     float *w32 = nullptr;     // [2][Dp][Dp]  W (re plane, im plane)
-    float *wt32 = nullptr;    // [2][Dp][Dp]  W^T (re plane, im plane)
-    float *partial = nullptr; // split-K slices of either product; GEMM2's sum X at slice 0
     float4 *rho_df[2] = {nullptr, nullptr};  // D x D {re_hi, re_lo, im_hi, im_lo}: rho, then V
     float4 *y_df = nullptr;                  // D x D stage buffer of the Strang step
     float4 *phase_df = nullptr;              // D: P_k as {re_hi, re_lo, im_hi, im_lo}
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
     float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
     int4 *in_tab = nullptr;                  // padded incoming table (rows with <= kInMax entries)
-    int partial_slices = 0;                  // split-K slices `partial` has room for
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
 };
 
 namespace {
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
-
-// ------------------------------------------------------------------ double-float
-// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, FMA-based TwoProd).
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ df df_add(df x, df y) {
-    df s = two_sum(x.hi, y.hi);
-    float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-    return fast_two_sum(s.hi, e);
-}
-
-__device__ __forceinline__ df df_add_f(df x, float y) {
-    df s = two_sum(x.hi, y);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, x.lo));
-}
-
-__device__ __forceinline__ df df_mul(df x, df y) {
-    float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
-
-struct cdf {
-    df re, im;
-};
-
-__device__ __forceinline__ cdf load_cdf(const float4 &v) { return {{v.x, v.y}, {v.z, v.w}}; }
-__device__ __forceinline__ float4 store_cdf(const cdf &c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
-
-__device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
-    return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
-}
-
-__device__ __forceinline__ cdf cdf_mul_conj(cdf a, cdf b) {  // a * conj(b)
-    return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.im, b.re), df_neg(df_mul(a.re, b.im)))};
-}
-
-// FP16 hi/lo pieces of a scaled double-float value, in FP32 arithmetic: x = hi + lo.
-__device__ __forceinline__ void df_to_half2(df x, float s, __half &h, __half &l) {
-    const float xs = x.hi * s;  // power-of-two scaling is exact
-    h = __float2half_rn(xs);
-    l = __float2half_rn(__fadd_rn(__fsub_rn(xs, __half2float(h)), x.lo * s));
-}
 
 // ------------------------------------------------------------------ set-up kernels
 __device__ __forceinline__ void split_half3(double x, __half &hi, __half &mid, __half &lo) {
@@ -197,21 +131,34 @@ __global__ void make_delta_kernel(int64_t D, const double2 *U, const double2 *P,
 }
 
 // a1 = [[Dre, Dim], [Dim, -Dre]] and b2 = [[Dre, Dim], [-Dim, Dre]] (2Dp x 2Dp) as three
-// FP16 planes (hi, mid, lo), about 33 significant bits.
+// FP16 planes (hi, mid, lo), about 33 significant bits.  b2's rows are GEMM2's output
+// columns; they are stored in groups of 128 = [the re rows of 64 consecutive n | the im rows
+// of the same n], so that one 128-wide output tile holds X_re and X_im of 64 columns.
 __global__ void static_planes_kernel(int64_t D, int64_t Dp, const double2 *Dl, double s, __half *a1, __half *b2) {
     const int64_t W2 = 2 * Dp;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= W2 * W2) return;
     int64_t r = idx / W2, c = idx % W2;
-    int64_t rk = r % Dp, cm = c % Dp;
-    bool rlo = r >= Dp, clo = c >= Dp;
+    int64_t cm = c % Dp;
+    bool clo = c >= Dp;
+    int64_t rk = r % Dp;                             // a1: row r = plane (r >= Dp), index r % Dp
+    bool rlo = r >= Dp;
+    int64_t rkb = 64 * (r / 128) + (r % 64);         // b2: column group r / 128, part (r % 128) / 64
+    bool rlob = (r % 128) >= 64;
     double va = 0.0, vb = 0.0;
     if (rk < D && cm < D) {
         double2 d = Dl[rk * D + cm];
-        if (!rlo && !clo) { va = d.x; vb = d.x; }
-        else if (!rlo && clo) { va = d.y; vb = d.y; }
-        else if (rlo && !clo) { va = d.y; vb = -d.y; }
-        else { va = -d.x; vb = d.x; }
+        if (!rlo && !clo) va = d.x;
+        else if (!rlo && clo) va = d.y;
+        else if (rlo && !clo) va = d.y;
+        else va = -d.x;
+    }
+    if (rkb < D && cm < D) {
+        double2 d = Dl[rkb * D + cm];
+        if (!rlob && !clo) vb = d.x;
+        else if (!rlob && clo) vb = d.y;
+        else if (rlob && !clo) vb = -d.y;
+        else vb = d.x;
     }
     __half h, md, l;
     split_half3(va * s, h, md, l);
@@ -291,96 +238,6 @@ __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
     if (idx >= D * D) return;
     const float4 v = st[idx];
     rho[idx] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
-}
-
-// W from the split-K partials of GEMM1 (rows r < Dp real, r >= Dp imaginary), in FP32:
-// writes W, its transpose (through a shared-memory tile so both stores coalesce) and its
-// FP16 hi/lo planes as GEMM2's A operand, row k = [W_re[k, :] | W_im[k, :]].  One block
-// per 32 x 32 tile of one instance.
-// Threads of w_reduce in y: each covers 32 / kWY rows of its 32 x 32 tile.
-constexpr int kWY = 16;
-
-__global__ void __launch_bounds__(32 * kWY) w_reduce_kernel(const TileItem *__restrict__ tiles,
-                                                            const InstDesc *__restrict__ descs) {
-    __shared__ float tre[32][33], tim[32][33];
-    // the work item and the descriptor are written once at set-up: read them while the
-    // previous kernel finishes
-    const TileItem it = tiles[blockIdx.x];
-    const InstDesc a = descs[it.inst];
-    pdl_wait();
-    pdl_trigger();
-    const int64_t Dp = a.Dp;
-    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x kWY
-    const int64_t k0 = (int64_t)it.by * 32, l0 = (int64_t)it.bx * 32;
-    const int64_t stride = 2 * Dp * Dp, plane = Dp * 2 * Dp;
-#pragma unroll
-    for (int q = 0; q < 32 / kWY; ++q) {
-        const int64_t k = k0 + ty + kWY * q, l = l0 + tx;
-        float re = 0.f, im = 0.f;
-        for (int s = 0; s < a.splits1; ++s) {
-            re += a.part[s * stride + k * Dp + l];
-            im += a.part[s * stride + (Dp + k) * Dp + l];
-        }
-        re *= a.inv_w;
-        im *= a.inv_w;
-        a.w32[k * Dp + l] = re;
-        a.w32[Dp * Dp + k * Dp + l] = im;
-        tre[ty + kWY * q][tx] = re;
-        tim[ty + kWY * q][tx] = im;
-        const float xr = re * a.s_w, xi = im * a.s_w;
-        __half h = __float2half_rn(xr);
-        a.w_pl[k * 2 * Dp + l] = h;
-        a.w_pl[plane + k * 2 * Dp + l] = __float2half_rn(xr - __half2float(h));
-        h = __float2half_rn(xi);
-        a.w_pl[k * 2 * Dp + Dp + l] = h;
-        a.w_pl[plane + k * 2 * Dp + Dp + l] = __float2half_rn(xi - __half2float(h));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 32 / kWY; ++q) {
-        const int64_t l = l0 + ty + kWY * q, k = k0 + tx;
-        a.wt32[l * Dp + k] = tre[tx][ty + kWY * q];
-        a.wt32[Dp * Dp + l * Dp + k] = tim[tx][ty + kWY * q];
-    }
-}
-
-// V_mn = P_m conj(P_n) (rho_mn + W_mn + conj(W_nm) + X_mn): the increment in FP32, the
-// sum and the phase in double-float.  One block per 32 x 8 elements of one instance.
-__global__ void __launch_bounds__(256) form_v_kernel(const TileItem *__restrict__ tiles,
-                                                     const InstDesc *__restrict__ descs) {
-    // set-up tables and the constant phases are read while the previous kernel finishes
-    const TileItem it = tiles[blockIdx.x];
-    const InstDesc a = descs[it.inst];
-    const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
-    const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
-    const bool inside = m < a.D && n < a.D;
-    const cdf pm = load_cdf(a.phase[inside ? m : 0]), pn = load_cdf(a.phase[inside ? n : 0]);
-    pdl_wait();
-    pdl_trigger();
-    if (!inside) return;
-    const int64_t Dp = a.Dp, stride = Dp * 2 * Dp;
-    const int splits = a.splits2;
-    // all loads issued before the first use
-    float pr[kMaxSlices], pi[kMaxSlices];
-#pragma unroll
-    for (int s = 0; s < kMaxSlices; ++s) {
-        pr[s] = s < splits ? __ldcg(a.part + s * stride + m * 2 * Dp + n) : 0.f;
-        pi[s] = s < splits ? __ldcg(a.part + s * stride + m * 2 * Dp + Dp + n) : 0.f;
-    }
-    const float wr = a.w32[m * Dp + n], wtr = a.wt32[m * Dp + n];
-    const float wi = a.w32[Dp * Dp + m * Dp + n], wti = a.wt32[Dp * Dp + m * Dp + n];
-    cdf r = load_cdf(a.rho[m * a.D + n]);
-    float xr = pr[0], xi = pi[0];
-#pragma unroll
-    for (int s = 1; s < kMaxSlices; ++s) {
-        xr += pr[s];
-        xi += pi[s];
-    }
-    const float ir = wr + wtr + xr * a.inv_x;
-    const float ii = wi - wti + xi * a.inv_x;
-    r.re = df_add_f(r.re, ir);
-    r.im = df_add_f(r.im, ii);
-    a.V[m * a.D + n] = store_cdf(cdf_mul(cdf_mul_conj(pm, pn), r));
 }
 
 // The Lindblad term of Eq. (3) as an update of the double-float buffers:
@@ -671,6 +528,8 @@ qed_status alloc(T **p, size_t count) {
 
 const TcSegs kSegs1 = {4, {0, 0, 1, 2, 0, 0}, {0, 1, 0, 0, 0, 0}};  // Delta(hi,mid,lo) x rho(hi,lo)
 const TcSegs kSegs2 = {3, {0, 1, 0, 0, 0, 0}, {0, 0, 1, 0, 0, 0}};  // W(hi,lo) x Delta(hi,mid,lo)
+const int kSeg1Pairs[8] = {0, 0, 0, 1, 1, 0, 2, 0};
+const int kSeg2Pairs[6] = {0, 0, 1, 0, 0, 1};
 
 template <class T>
 qed_status upload(T **dst, const std::vector<T> &v) {
@@ -679,9 +538,20 @@ qed_status upload(T **dst, const std::vector<T> &v) {
     return QED_OK;
 }
 
+// The plans of a model's two products: GEMM1 [W_re; W_im] = A1 . rho^T (2Dp x Dp, K 2Dp, four
+// plane pairs), GEMM2 [X_re | X_im] = W . B2^T (Dp x 2Dp, K 2Dp, three plane pairs) with
+// 128-wide tiles.  splits = CTAs per cluster (on-chip reduction of the split-K slices).
+bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, int splits2) {
+    const int Dp = (int)S.Dp;
+    return tc_gemm_plan(g1, S.a1, 3, S.rho_pl, 2, 2 * Dp, Dp, 2 * Dp, 4, kSeg1Pairs, S.num_sms, splits1, bn1, true) &&
+           tc_gemm_plan(g2, S.w_pl, 2, S.b2, 3, Dp, 2 * Dp, 2 * Dp, 3, kSeg2Pairs, S.num_sms, splits2, 128, true);
+}
+
 // Descriptors, jobs and work lists of a batch.  With `single` set (one model on its own)
-// the GEMMs keep their split-K slices; in a batch every product runs unsplit, largest
-// first, since the batch itself fills the GPU.
+// the products keep their plans (split-K slices reduced inside clusters); in a batch every
+// product runs unsplit, largest first, since the batch itself fills the GPU.  GEMM1 skips
+// tiles that lie wholly in the zero padding (rows or columns >= D); GEMM2 runs the tiles on
+// or above the diagonal only (its epilogue writes both halves of the Hermitian V).
 qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
     b.release();
     b.n = n;
@@ -695,26 +565,15 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
     std::vector<GemmJob> jobs1((size_t)n), jobs2((size_t)n);
     std::vector<CUtensorMap> maps((size_t)(4 * n));
     std::vector<GemmItem> it1, it2;
-    std::vector<TileItem> wt, et;
+    std::vector<TileItem> et;
     for (int i = 0; i < n; ++i) {
         qed_model *m = ms[i];
         SplitState &S = *m->sp;
         InstDesc &d = desc[(size_t)i];
-        d.D = m->D;
-        d.Dp = S.Dp;
-        d.splits1 = single ? S.g1.splits : 1;  // split-K slices summed by w_reduce
-        d.splits2 = single ? S.g2.splits : 1;  // and by form_v
-        if (d.splits1 > kMaxSlices || d.splits2 > kMaxSlices) {
-            set_error("split step: more split-K slices than the element-wise kernels sum");
-            return QED_EINVAL;
-        }
-        d.inv_w = (float)(1.0 / (S.scale_delta * S.scale_rho));
-        d.s_w = (float)S.scale_w;
-        d.inv_x = (float)(1.0 / (S.scale_w * S.scale_delta));
+        const int64_t D = m->D, Dp = S.Dp;
+        d.D = D;
+        d.Dp = Dp;
         d.s_rho = (float)S.scale_rho;
-        d.part = S.partial;
-        d.w32 = S.w32;
-        d.wt32 = S.wt32;
         d.rho = S.rho_df[0];
         d.V = S.rho_df[1];
         d.Y = S.y_df;
@@ -726,16 +585,13 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.coef = S.coef_df;
         d.in_tab = S.in_tab;
         d.rho_pl = S.rho_pl;
-        d.w_pl = S.w_pl;
-        // a model on its own keeps its plans; in a batch every product runs unsplit with the
-        // wide tile, so one grouped launch serves all instances
         TcGemm bg1 = S.g1, bg2 = S.g2;
-        if (!single) {
-            const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
-            const int seg2[6] = {0, 0, 1, 0, 0, 1};
-            if (!tc_gemm_plan(bg1, S.a1, 3, S.rho_pl, 2, S.g1.M, S.g1.N, S.g1.K, 4, seg1, 1, 1, kTcBNMax) ||
-                !tc_gemm_plan(bg2, S.w_pl, 2, S.b2, 3, S.g2.M, S.g2.N, S.g2.K, 3, seg2, 1, 1, kTcBNMax))
-                return QED_ECUDA;
+        if (!single && !plan_products(S, bg1, bg2, 1, kTcBNMax, 1)) return QED_ECUDA;
+        auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+        if (!pow2(bg1.splits) || bg1.splits > kTcMaxCluster || !pow2(bg2.splits) || bg2.splits > kTcMaxClusterV ||
+            bg2.bn != 128) {
+            set_error("split step: product plan outside the cluster epilogue's limits");
+            return QED_EINVAL;
         }
         maps[(size_t)(4 * i + 0)] = bg1.a;
         maps[(size_t)(4 * i + 1)] = bg1.b;
@@ -743,46 +599,60 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         maps[(size_t)(4 * i + 3)] = bg2.b;
         const TcGemm *gs[2] = {&bg1, &bg2};
         GemmJob *js[2] = {&jobs1[(size_t)i], &jobs2[(size_t)i]};
-        std::vector<GemmItem> *its[2] = {&it1, &it2};
         for (int q = 0; q < 2; ++q) {
             const TcGemm &g = *gs[q];
-            const int splits = single ? g.splits : 1;
-            const int kb_total = g.nseg * (g.K / kTcBK);
-            js[q]->M = g.M;
-            js[q]->N = g.N;
-            js[q]->kb_per_seg = g.K / kTcBK;
-            js[q]->kb_per_split = single ? g.kb_per_split : kb_total;
-            js[q]->out = S.partial;
-            js[q]->tx_bytes = kTcBM * kTcBK * 2 + g.b_box_rows * kTcBK * 2;
-            // an unsplit GEMM1 writes W, W^T and the W planes itself; split products
-            // leave their slices to w_reduce / form_v
-            js[q]->mode = q == 0 && splits == 1 ? kEpiW : kEpiPlain;
-            js[q]->w = TcEpilogueW();
-            if (js[q]->mode == kEpiW) {
-                js[q]->w.Dp = S.Dp;
-                js[q]->w.inv_w = d.inv_w;
-                js[q]->w.s_w = d.s_w;
-                js[q]->w.w32 = S.w32;
-                js[q]->w.wt32 = S.wt32;
-                js[q]->w.w_pl = S.w_pl;
+            GemmJob &j = *js[q];
+            j.M = g.M;
+            j.N = g.N;
+            j.kb_per_seg = g.K / kTcBK;
+            j.kb_per_split = g.kb_per_split;
+            j.out = nullptr;
+            j.mode = q == 0 ? kEpiW : kEpiV;
+            j.tx_bytes = tc_stage_tx_bytes(g, j.mode);
+            j.epi = TcEpilogue();
+            j.epi.D = D;
+            j.epi.Dp = Dp;
+            j.epi.w32 = S.w32;
+            if (q == 0) {
+                j.epi.inv = (float)(1.0 / (S.scale_delta * S.scale_rho));
+                j.epi.s_w = (float)S.scale_w;
+                j.epi.w_pl = S.w_pl;
+            } else {
+                j.epi.inv = (float)(1.0 / (S.scale_w * S.scale_delta));
+                j.epi.rho = S.rho_df[0];
+                j.epi.phase = S.phase_df;
+                j.epi.V = S.rho_df[1];
             }
-            // the slices of one tile are consecutive: they form one cluster
-            for (int tm = 0; tm < g.M / kTcBM; ++tm)
-                for (int tn = 0; tn < (g.N + g.bn - 1) / g.bn; ++tn)
-                    for (int sp = 0; sp < splits; ++sp) its[q]->push_back({i, tm, tn, sp});
             if (i == 0) {
-                (q == 0 ? b.cs1 : b.cs2) = splits;
+                (q == 0 ? b.cs1 : b.cs2) = g.splits;
                 (q == 0 ? b.bn1 : b.bn2) = g.bn;
+            } else if (g.splits != (q == 0 ? b.cs1 : b.cs2) || g.bn != (q == 0 ? b.bn1 : b.bn2)) {
+                set_error("batched evolution: every instance of a launch needs the same tile plan");
+                return QED_EINVAL;
             }
-            if (q == 0 && splits > 1) b.w_reduce = true;
         }
-        for (int by = 0; by < S.Dp / 32; ++by)
-            for (int bx = 0; bx < S.Dp / 32; ++bx) wt.push_back({i, bx, by, 0});
-        for (int by = 0; by < (m->D + 7) / 8; ++by)
-            for (int bx = 0; bx < (m->D + 31) / 32; ++bx) et.push_back({i, bx, by, 0});
+        // GEMM1 tiles: 128 rows of [W_re; W_im] x bn1 columns; wholly-padding tiles skipped
+        for (int tm = 0; tm < bg1.M / kTcBM; ++tm) {
+            if ((tm * kTcBM) % Dp >= D) continue;
+            for (int tn = 0; tn * bg1.bn < bg1.N; ++tn) {
+                if ((int64_t)tn * bg1.bn >= D) continue;
+                for (int sp = 0; sp < bg1.splits; ++sp) it1.push_back({i, tm, tn, sp});
+            }
+        }
+        // GEMM2 tiles: 128 rows m x 64 complex columns n, on or above the diagonal
+        for (int tm = 0; tm < bg2.M / kTcBM; ++tm) {
+            if ((int64_t)tm * kTcBM >= D) continue;
+            for (int tj = 2 * tm; tj < bg2.N / 128; ++tj) {
+                if ((int64_t)tj * 64 >= D) continue;
+                for (int sp = 0; sp < bg2.splits; ++sp) it2.push_back({i, tm, tj, sp});
+            }
+        }
+        for (int by = 0; by < (D + 7) / 8; ++by)
+            for (int bx = 0; bx < (D + 31) / 32; ++bx) et.push_back({i, bx, by, 0});
     }
     if (!single) {
-        // longest products first, so the tail of the grouped launch is short
+        // longest products first, so the tail of the grouped launch is short (unsplit:
+        // every item is a cluster of one)
         auto by_cost = [&](const GemmItem &x, const GemmItem &y) {
             return jobs1[(size_t)x.job].kb_per_seg > jobs1[(size_t)y.job].kb_per_seg;
         };
@@ -801,29 +671,39 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
     SPLIT_TRY(upload(&b.jobs2, jobs2));
     SPLIT_TRY(upload(&b.items1, it1));
     SPLIT_TRY(upload(&b.items2, it2));
-    SPLIT_TRY(upload(&b.wtiles, wt));
     SPLIT_TRY(upload(&b.etiles, et));
     b.n_items1 = (int)it1.size();
     b.n_items2 = (int)it2.size();
-    b.n_wtiles = (int)wt.size();
     b.n_etiles = (int)et.size();
+    if (single) {
+        SplitState &S = *ms[0]->sp;
+        b.single = true;
+        b.D = ms[0]->D;
+        b.g1 = S.g1;
+        b.g2 = S.g2;
+        b.j1 = jobs1[0];
+        b.j2 = jobs2[0];
+        if (tc_gemm_single_ctas(b.g1, kEpiW, b.D) * 1 != b.n_items1 ||
+            tc_gemm_single_ctas(b.g2, kEpiV, b.D) != b.n_items2) {
+            set_error("split step: tile lists of the single-model launch disagree");
+            return QED_ECUDA;
+        }
+    }
     if (!tc_gemm_prepare_grouped()) return QED_ECUDA;
     return QED_OK;
 }
 
 void launch_gemm1(const Batch &b, uint32_t *err, cudaStream_t s) {
-    tc_gemm_grouped_launch(b.items1, b.n_items1, b.jobs1, kSegs1, b.bn1, err, s);
+    if (b.single)
+        tc_gemm_single_launch(b.g1, b.j1, kSegs1, b.D, err, s);
+    else
+        tc_gemm_grouped_launch(b.items1, b.n_items1, b.jobs1, kSegs1, b.bn1, kEpiW, b.cs1, err, s);
 }
 void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
-    tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, err, s);
-}
-void launch_w_reduce(const Batch &b, cudaStream_t s) {
-    launch_pdl(w_reduce_kernel, dim3(b.n_wtiles), dim3(32, kWY), 0, s, b.wtiles, b.desc);
-    count_launches(1);
-}
-void launch_form(const Batch &b, cudaStream_t s) {
-    launch_pdl(form_v_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
-    count_launches(1);
+    if (b.single)
+        tc_gemm_single_launch(b.g2, b.j2, kSegs2, b.D, err, s);
+    else
+        tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, kEpiV, b.cs2, err, s);
 }
 void launch_dissipate(const Batch &b, cudaStream_t s) {
     launch_pdl(dissipate_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
@@ -862,24 +742,17 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         SPLIT_TRY(alloc(&S.rho_pl, pl));
         SPLIT_TRY(alloc(&S.w_pl, pl));
         SPLIT_TRY(alloc(&S.w32, (size_t)2 * Dp * Dp));
-        SPLIT_TRY(alloc(&S.wt32, (size_t)2 * Dp * Dp));
         SPLIT_TRY(alloc(&S.rho_df[0], (size_t)(D * D)));
         SPLIT_TRY(alloc(&S.rho_df[1], (size_t)(D * D)));
         SPLIT_TRY(alloc(&S.y_df, (size_t)(D * D)));
         SPLIT_TRY(alloc(&S.phase_df, (size_t)D));
+        // zero padding: tiles of GEMM1 that lie wholly in it are never written
         QED_CUDA_TRY(cudaMemset(S.rho_pl, 0, pl * sizeof(__half)));
         QED_CUDA_TRY(cudaMemset(S.w_pl, 0, pl * sizeof(__half)));
-        // GEMM1: Delta (hi, mid, lo) x rho (hi, lo): hi*hi + hi*lo + mid*hi + lo*hi
-        const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
-        // GEMM2: W (hi, lo) x Delta (hi, mid, lo): hi*hi + lo*hi + hi*mid
-        const int seg2[6] = {0, 0, 1, 0, 0, 1};
-        static_assert(kTcMaxSeg >= 4, "segment lists");
-        if (!tc_gemm_plan(S.g1, S.a1, 3, S.rho_pl, 2, (int)(2 * Dp), (int)Dp, (int)(2 * Dp), 4, seg1, S.num_sms))
-            return QED_ECUDA;
-        if (!tc_gemm_plan(S.g2, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp), (int)(2 * Dp), 3, seg2, S.num_sms))
-            return QED_ECUDA;
-        S.partial_slices = std::max(S.g1.splits, S.g2.splits);
-        SPLIT_TRY(alloc(&S.partial, (size_t)S.partial_slices * 2 * Dp * Dp));
+        QED_CUDA_TRY(cudaMemset(S.w32, 0, (size_t)2 * Dp * Dp * sizeof(float)));
+        // the planner's split-K factors become the cluster sizes of the on-chip reduction
+        static_assert(kTcMaxAutoSplits <= kTcMaxCluster, "plans must fit the cluster epilogues");
+        if (!plan_products(S, S.g1, S.g2, 0, 0, 0)) return QED_ECUDA;
 
         // per-row phases P_k as double-floats
         std::vector<double2> ph((size_t)D);
@@ -974,10 +847,8 @@ void split_check_density(qed_model *m, const double2 *rho, cudaStream_t s) {
 
 void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
     if (b.scheme == QED_SCHEME_STRANG) launch_half_lindblad(b, 0, 1, s);  // rho <- E(dt/2) rho
-    launch_gemm1(b, err, s);  // unsplit: its epilogue writes W, W^T and the W planes
-    if (b.w_reduce) launch_w_reduce(b, s);
-    launch_gemm2(b, err, s);
-    launch_form(b, s);
+    launch_gemm1(b, err, s);  // W and its planes (split-K slices summed inside each cluster)
+    launch_gemm2(b, err, s);  // X on and above the diagonal; its epilogue writes V = U rho U^+
     if (b.scheme == QED_SCHEME_STRANG)
         launch_half_lindblad(b, 1, 0, s);  // rho <- E(dt/2) V
     else
@@ -986,43 +857,37 @@ void batch_step(const Batch &b, uint32_t *err, cudaStream_t s) {
 
 void split_step(qed_model *m, cudaStream_t s) { batch_step(m->sp->self, m->err, s); }
 
-// Chooses the tile width and split-K factor of each of the model's two products by timing
-// whole steps (so the slice reductions the split products need are part of the cost):
-// GEMM1's candidates with GEMM2 as planned, then GEMM2's with the best GEMM1.  Candidates:
-// 128- and 256-wide tiles, 1, 2 or 4 slices.  Overwrites the internal state (qed_evolve
-// imports rho again) and replaces the step tables; the caller drops its captured graphs.
+// Chooses the tile width and split-K factor (CTAs per cluster) of each of the model's two
+// products by timing whole steps: GEMM1's candidates (128- and 256-wide tiles, 1, 2, 4 or 8
+// slices) with GEMM2 as planned, then GEMM2's (128-wide, 1, 2 or 4 slices) with the best
+// GEMM1.  Plans whose slices would not be a power of two are skipped.  Overwrites the
+// internal state (qed_evolve imports rho again) and replaces the step tables; the caller
+// drops its captured graphs.
 qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &choice) {
     SplitState &S = *m->sp;
-    const int64_t Dp = S.Dp;
-    if (S.partial_slices < kTcMaxAutoSplits) {
-        QED_CUDA_TRY(cudaStreamSynchronize(s));
-        cudaFree(S.partial);
-        S.partial = nullptr;
-        SPLIT_TRY(alloc(&S.partial, (size_t)kTcMaxAutoSplits * 2 * Dp * Dp));
-        S.partial_slices = kTcMaxAutoSplits;
-    }
     qed_model *self[1] = {m};
-    const int seg1[8] = {0, 0, 0, 1, 1, 0, 2, 0};
-    const int seg2[6] = {0, 0, 1, 0, 0, 1};
     auto candidates = [&](int which, std::vector<TcGemm> &out) -> qed_status {
-        for (int bn : {128, 256})
-            for (int sp : {1, 2, 4}) {
-                TcGemm g;
-                const bool ok = which == 1 ? tc_gemm_plan(g, S.a1, 3, S.rho_pl, 2, (int)(2 * Dp), (int)Dp,
-                                                          (int)(2 * Dp), 4, seg1, S.num_sms, sp, bn)
-                                           : tc_gemm_plan(g, S.w_pl, 2, S.b2, 3, (int)Dp, (int)(2 * Dp),
-                                                          (int)(2 * Dp), 3, seg2, S.num_sms, sp, bn);
-                if (!ok) return QED_ECUDA;
-                bool seen = false;
+        for (int bn : {128, 256}) {
+            if (which == 2 && bn != 128) continue;
+            for (int sp : {1, 2, 4, 8}) {
+                if (which == 2 && sp > kTcMaxClusterV) continue;
+                TcGemm g1, g2;
+                if (!plan_products(S, g1, g2, which == 1 ? sp : S.g1.splits, which == 1 ? bn : S.g1.bn,
+                                   which == 2 ? sp : S.g2.splits))
+                    return QED_ECUDA;
+                const TcGemm &g = which == 1 ? g1 : g2;
+                bool seen = (g.splits & (g.splits - 1)) != 0;
                 for (const auto &h : out) seen = seen || (h.bn == g.bn && h.splits == g.splits);
                 if (!seen) out.push_back(g);
             }
+        }
         return QED_OK;
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     QED_CUDA_TRY(cudaEventCreate(&e0));
     QED_CUDA_TRY(cudaEventCreate(&e1));
     auto time_steps = [&](float &ms) -> qed_status {
+        QED_CUDA_TRY(cudaStreamSynchronize(s));
         SPLIT_TRY(build_batch(S.self, self, 1, true));
         for (int i = 0; i < 2; ++i) batch_step(S.self, m->err, s);
         QED_CUDA_TRY(cudaEventRecord(e0, s));
@@ -1057,6 +922,7 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
     S.g1 = g1;
     S.g2 = g2;
     if (st != QED_OK) return st;
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
     SPLIT_TRY(build_batch(S.self, self, 1, true));
     choice = "gemm1 " + std::to_string(g1.bn) + "-wide x" + std::to_string(g1.splits) + " slices, gemm2 " +
              std::to_string(g2.bn) + "-wide x" + std::to_string(g2.splits) + " slices, " +
@@ -1079,32 +945,24 @@ int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
         cudaEventRecord(m->ev[e++], s);
         launch_gemm1(b, m->err, s);
         cudaEventRecord(m->ev[e++], s);
-        if (b.w_reduce) launch_w_reduce(b, s);
-        cudaEventRecord(m->ev[e++], s);
         launch_gemm2(b, m->err, s);
-        cudaEventRecord(m->ev[e++], s);
-        launch_form(b, s);
         cudaEventRecord(m->ev[e++], s);
         launch_lindblad(b, 1, 1, 2, 0.25f, 0, s);
         cudaEventRecord(m->ev[e++], s);
         launch_lindblad(b, 2, 1, 0, 0.5f, 0, s);
         cudaEventRecord(m->ev[e++], s);
-        label = "lindblad_a,lindblad_b,gemm1_tc,w_reduce,gemm2_tc,form_v,lindblad_c,lindblad_d";
-        return 8;
+        label = "lindblad_a,lindblad_b,gemm1_tc,gemm2_tc_v,lindblad_c,lindblad_d";
+        return 6;
     }
     cudaEventRecord(m->ev[0], s);
     launch_gemm1(b, m->err, s);
     cudaEventRecord(m->ev[1], s);
-    if (b.w_reduce) launch_w_reduce(b, s);
-    cudaEventRecord(m->ev[2], s);
     launch_gemm2(b, m->err, s);
-    cudaEventRecord(m->ev[3], s);
-    launch_form(b, s);
-    cudaEventRecord(m->ev[4], s);
+    cudaEventRecord(m->ev[2], s);
     launch_dissipate(b, s);
-    cudaEventRecord(m->ev[5], s);
-    label = "gemm1_tc,w_reduce,gemm2_tc,form_v,dissipate";
-    return 5;
+    cudaEventRecord(m->ev[3], s);
+    label = "gemm1_tc,gemm2_tc_v,dissipate";
+    return 3;
 }
 
 void split_renorm(qed_model *m, cudaStream_t s) {
@@ -1174,9 +1032,8 @@ void split_release(qed_model *m) {
     if (!m->sp) return;
     SplitState &S = *m->sp;
     S.self.release();
-    void *ptrs[] = {S.a1,        S.b2,        S.rho_pl,   S.w_pl,    S.w32,     S.wt32,
-                    S.partial,   S.rho_df[0], S.rho_df[1], S.phase_df, S.damp_df, S.coef_df, S.in_tab,
-                    S.y_df};
+    void *ptrs[] = {S.a1,       S.b2,       S.rho_pl,   S.w_pl,    S.w32,    S.rho_df[0], S.rho_df[1],
+                    S.phase_df, S.damp_df, S.coef_df, S.in_tab, S.y_df};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m->sp;
