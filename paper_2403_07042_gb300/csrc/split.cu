@@ -54,7 +54,7 @@ constexpr int kNoJump = 0x7fffffff;
 // Pairs of incoming lists longer than this in total are merged by the whole warp.
 constexpr int kLongMerge = 32;
 
-// 32 x 8 element blocks (the Lindblad kernels) of one instance
+// 32 x (8 kRows) element blocks (the Lindblad kernels) of one instance
 struct TileItem {
     int inst, bx, by, pad;
 };
@@ -304,98 +304,17 @@ __device__ __noinline__ bool long_merge_df(int64_t D, const int32_t *in_jump, co
     return is_long;
 }
 
+// Rows of one element block: a block of 32 x 8 threads updates 32 columns and 8 kRows rows;
+// thread (x, y) takes the rows 8 r + y, r < kRows, of its column, so the column's jump
+// entries are read once for kRows elements and their loads are in flight together.
+constexpr int kRows = 2;
+
+// The output of one element: out = B + f (dt L(X))_mn with the accumulated increment (gr, gi),
+// written as a double-float, and its FP16 planes when asked for.
 template <bool LIE>
-__device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ tiles,
-                                                const InstDesc *__restrict__ descs, int xsel, int bsel, int osel,
-                                                float f, bool planes) {
-    // set-up tables (damping, padded jump rows) are read while the previous kernel finishes
-    const TileItem it = tiles[blockIdx.x];
-    const InstDesc a = descs[it.inst];
+__device__ __forceinline__ void lindblad_store(const InstDesc &a, float4 *O, int64_t m, int64_t n, const cdf &b,
+                                               float f, float gr, float gi, bool planes) {
     const int64_t D = a.D;
-    const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
-    const int64_t m = (int64_t)it.by * 8 + threadIdx.y;
-    const bool inside = m < D && n < D;
-    const int64_t mc = inside ? m : 0, nc = inside ? n : 0;
-    const float2 dm = a.damp[mc], dn = a.damp[nc];
-    // the row's padded jump entries are the same for the whole warp (one m per warp): read
-    // them before the wait; the column's entries after it, to keep the register count low
-    int4 em[kInMax], en[kInMax];
-    if (a.in_tab) {
-#pragma unroll
-        for (int i = 0; i < kInMax; ++i) em[i] = a.in_tab[mc * kInMax + i];
-    }
-    const float4 *X = LIE ? a.V : state_buf(a, xsel);
-    const float4 *B = LIE ? a.V : state_buf(a, bsel);
-    float4 *O = LIE ? a.rho : state_buf(a, osel);
-    pdl_wait();
-    pdl_trigger();
-    // lanes outside the matrix stay to the end (with clamped indices, no stores): the warp
-    // shares the merge of long jump lists below
-    const cdf v = load_cdf(X[mc * D + nc]);
-    if (a.in_tab) {
-#pragma unroll
-        for (int i = 0; i < kInMax; ++i) en[i] = a.in_tab[nc * kInMax + i];
-    }
-    const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
-    float gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
-    float gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
-    if (a.in_tab) {
-        // padded rows: pairs of equal jumps, every gather issued before the first use
-        float4 u[kInMax];
-        float2 cq[kInMax];
-        bool hit[kInMax];
-#pragma unroll
-        for (int i = 0; i < kInMax; ++i) {
-            int src = 0;
-            float2 c2 = make_float2(0.f, 0.f);
-            bool h = false;
-#pragma unroll
-            for (int j = 0; j < kInMax; ++j)
-                if (en[j].x == em[i].x) {
-                    h = true;
-                    src = en[j].y;
-                    c2 = make_float2(__int_as_float(en[j].z), __int_as_float(en[j].w));
-                }
-            hit[i] = h && em[i].x != kNoJump;
-            cq[i] = c2;
-            u[i] = hit[i] ? X[(int64_t)em[i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int i = 0; i < kInMax; ++i) {
-            if (!hit[i]) continue;
-            const df c = df_mul({__int_as_float(em[i].z), __int_as_float(em[i].w)}, {cq[i].x, cq[i].y});
-            const float ur = u[i].x + u[i].y, ui = u[i].z + u[i].w;
-            gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
-            gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
-        }
-    }
-    const bool lists = !a.in_tab && inside;
-    int p = lists ? a.in_ptr[m] : 0, pe = lists ? a.in_ptr[m + 1] : 0;
-    int q = lists ? a.in_ptr[n] : 0, qe = lists ? a.in_ptr[n + 1] : 0;
-    if (!a.in_tab) {
-        // long lists: merged by the whole warp
-        const bool is_long = long_merge_df(D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
-        if (is_long) pe = p;  // done: skip the serial merge
-    }
-    while (p < pe && q < qe) {  // jumps present in both incoming lists
-        const int jp = a.in_jump[p], jq = a.in_jump[q];
-        if (jp < jq) {
-            ++p;
-        } else if (jp > jq) {
-            ++q;
-        } else {
-            const float2 cp = a.coef[p], cq = a.coef[q];
-            const df c = df_mul({cp.x, cp.y}, {cq.x, cq.y});  // dt c_j(m) c_j(n)
-            const float4 u = X[(int64_t)a.in_src[p] * D + a.in_src[q]];
-            const float ur = u.x + u.y, ui = u.z + u.w;
-            gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
-            gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
-            ++p;
-            ++q;
-        }
-    }
-    if (!inside) return;
-    const cdf b = LIE ? v : load_cdf(B[m * D + n]);
     cdf out;
     out.re = df_add_f(b.re, LIE ? gr : f * gr);
     out.im = df_add_f(b.im, LIE ? gi : f * gi);
@@ -411,14 +330,141 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     a.rho_pl[plane + m * 2 * a.Dp + a.Dp + n] = l;
 }
 
+// -(d_m + d_n) dt/2 X_mn in FP32 (d from the double-float damping table)
+__device__ __forceinline__ void damping_term(float2 dm, float2 dn, const cdf &v, float &gr, float &gi) {
+    const df dl = df_add({dm.x, dm.y}, {dn.x, dn.y});
+    gr = -__fmaf_rn(dl.hi, v.re.hi, __fmaf_rn(dl.hi, v.re.lo, dl.lo * v.re.hi));
+    gi = -__fmaf_rn(dl.hi, v.im.hi, __fmaf_rn(dl.hi, v.im.lo, dl.lo * v.im.hi));
+}
+
+template <bool LIE>
+__device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ tiles,
+                                                const InstDesc *__restrict__ descs, int xsel, int bsel, int osel,
+                                                float f, bool planes) {
+    // set-up tables (damping, padded jump rows) are read while the previous kernel finishes
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc a = descs[it.inst];
+    const int64_t D = a.D;
+    const int64_t n = (int64_t)it.bx * 32 + threadIdx.x;
+    const int64_t m0 = (int64_t)it.by * (8 * kRows) + threadIdx.y;
+    const bool n_in = n < D;
+    const int64_t nc = n_in ? n : 0;
+    const float2 dn = a.damp[nc];
+    const float4 *X = LIE ? a.V : state_buf(a, xsel);
+    const float4 *B = LIE ? a.V : state_buf(a, bsel);
+    float4 *O = LIE ? a.rho : state_buf(a, osel);
+    if (a.in_tab) {
+        // padded incoming tables: the row entries are the same for the whole warp (one row per
+        // warp and r), the column's for all kRows rows of the thread
+        int4 en[kInMax], em[kRows][kInMax];
+        float2 dm[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r, mc = m < D ? m : 0;
+            dm[r] = a.damp[mc];
+#pragma unroll
+            for (int i = 0; i < kInMax; ++i) em[r][i] = a.in_tab[mc * kInMax + i];
+        }
+#pragma unroll
+        for (int i = 0; i < kInMax; ++i) en[i] = a.in_tab[nc * kInMax + i];
+        pdl_wait();
+        pdl_trigger();
+        // every load of the kRows elements issued before the first use
+        float4 v[kRows], u[kRows][kInMax];
+        float2 cq[kRows][kInMax];
+        bool hit[kRows][kInMax];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r;
+            const bool inside = m < D && n_in;
+            v[r] = X[(inside ? m : 0) * D + nc];
+#pragma unroll
+            for (int i = 0; i < kInMax; ++i) {
+                int src = 0;
+                float2 c2 = make_float2(0.f, 0.f);
+                bool h = false;
+#pragma unroll
+                for (int j = 0; j < kInMax; ++j)
+                    if (en[j].x == em[r][i].x) {
+                        h = true;
+                        src = en[j].y;
+                        c2 = make_float2(__int_as_float(en[j].z), __int_as_float(en[j].w));
+                    }
+                hit[r][i] = h && em[r][i].x != kNoJump && inside;
+                cq[r][i] = c2;
+                u[r][i] = hit[r][i] ? X[(int64_t)em[r][i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r;
+            if (!(m < D && n_in)) continue;
+            const cdf vv = load_cdf(v[r]);
+            float gr, gi;
+            damping_term(dm[r], dn, vv, gr, gi);
+#pragma unroll
+            for (int i = 0; i < kInMax; ++i) {
+                if (!hit[r][i]) continue;
+                const df c = df_mul({__int_as_float(em[r][i].z), __int_as_float(em[r][i].w)}, {cq[r][i].x, cq[r][i].y});
+                const float ur = u[r][i].x + u[r][i].y, ui = u[r][i].z + u[r][i].w;
+                gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
+                gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
+            }
+            const cdf b = LIE ? vv : load_cdf(B[m * D + n]);
+            lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
+        }
+        return;
+    }
+    pdl_wait();
+    pdl_trigger();
+    // incoming lists: the rows one after another; lanes outside the matrix stay to the end of
+    // every row (with clamped indices, no stores), since the warp shares the merge of long
+    // jump lists
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+        const int64_t m = m0 + 8 * r;
+        const bool inside = m < D && n_in;
+        const int64_t mc = inside ? m : 0;
+        const float2 dm = a.damp[m < D ? m : 0];
+        const cdf v = load_cdf(X[mc * D + nc]);
+        float gr, gi;
+        damping_term(dm, dn, v, gr, gi);
+        int p = inside ? a.in_ptr[m] : 0, pe = inside ? a.in_ptr[m + 1] : 0;
+        int q = inside ? a.in_ptr[n] : 0, qe = inside ? a.in_ptr[n + 1] : 0;
+        // long lists: merged by the whole warp
+        const bool is_long = long_merge_df(D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
+        if (is_long) pe = p;  // done: skip the serial merge
+        while (p < pe && q < qe) {  // jumps present in both incoming lists
+            const int jp = a.in_jump[p], jq = a.in_jump[q];
+            if (jp < jq) {
+                ++p;
+            } else if (jp > jq) {
+                ++q;
+            } else {
+                const float2 cp = a.coef[p], cqq = a.coef[q];
+                const df c = df_mul({cp.x, cp.y}, {cqq.x, cqq.y});  // dt c_j(m) c_j(n)
+                const float4 uu = X[(int64_t)a.in_src[p] * D + a.in_src[q]];
+                const float ur = uu.x + uu.y, ui = uu.z + uu.w;
+                gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
+                gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
+                ++p;
+                ++q;
+            }
+        }
+        if (!inside) continue;
+        const cdf b = LIE ? v : load_cdf(B[m * D + n]);
+        lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
+    }
+}
+
 // Lie step: rho = V + dt L(V), and the next planes.
-__global__ void __launch_bounds__(256, 4) dissipate_df_kernel(const TileItem *__restrict__ tiles,
+__global__ void __launch_bounds__(256, 2) dissipate_df_kernel(const TileItem *__restrict__ tiles,
                                                            const InstDesc *__restrict__ descs) {
     lindblad_update<true>(tiles, descs, 1, 1, 0, 1.f, true);
 }
 
 // One stage of the Strang step: out = B + f dt L(X).
-__global__ void __launch_bounds__(256, 4) lindblad_df_kernel(const TileItem *__restrict__ tiles,
+__global__ void __launch_bounds__(256, 2) lindblad_df_kernel(const TileItem *__restrict__ tiles,
                                                           const InstDesc *__restrict__ descs, int xsel, int bsel,
                                                           int osel, float f, int planes) {
     lindblad_update<false>(tiles, descs, xsel, bsel, osel, f, planes != 0);
@@ -647,7 +693,7 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
                 for (int sp = 0; sp < bg2.splits; ++sp) it2.push_back({i, tm, tj, sp});
             }
         }
-        for (int by = 0; by < (D + 7) / 8; ++by)
+        for (int by = 0; by < (D + 8 * kRows - 1) / (8 * kRows); ++by)
             for (int bx = 0; bx < (D + 31) / 32; ++bx) et.push_back({i, bx, by, 0});
     }
     if (!single) {
