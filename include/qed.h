@@ -296,6 +296,26 @@ qed_status qed_set_U(qed_model *m, const void *U, qed_stream stream);
 qed_status qed_get_U(const qed_model *m, void *U, qed_stream stream);
 
 /*
+ * Wait-gate test hook (the paper has no counterpart: it exercises this library's own error
+ * path).  With closed != 0 the tensor-core kernels of m's split-precision step first wait,
+ * for at most budget_cycles SM clock cycles, for a device flag to clear - a flag that nothing
+ * clears - before they issue any load or product.  When that wait runs out a kernel records
+ * the timeout and skips its work (the step's result is then meaningless) and the next
+ * qed_sync_status returns QED_ETIMEOUT; the model stays usable.  closed = 0 removes the
+ * wait.  Drops the captured step graphs; synchronises `stream`.  EINVAL for a negative
+ * budget, EUNSUPPORTED for FP64 models (that path has no bounded waits).
+ */
+qed_status qed_set_wait_gate(qed_model *m, int32_t closed, int64_t budget_cycles, qed_stream stream);
+
+/*
+ * Allocation-failure test hook (process-wide; the paper has no counterpart): from now on the
+ * library's device allocations fail as on an exhausted device (the call that needed them
+ * returns QED_ENOMEM and frees what it had allocated) once they would exceed `bytes` bytes
+ * in total; bytes < 0 removes the limit.
+ */
+qed_status qed_set_alloc_budget(int64_t bytes);
+
+/*
  * Run n_steps steps like qed_evolve (no records), timing each kernel class with CUDA
  * events on `stream`; writes the mean duration in milliseconds per step of each class
  * into ms[0..n_kernels-1] and the class names (comma separated) into names (size

@@ -93,6 +93,8 @@ def lib():
                               ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
         "qed_tc_gemm": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
         "qed_tc_gemm_static": [vp, i32, vp, i32, i32, i32, i32, i32, _c_int32_p, i32, vp, vp],
+        "qed_set_wait_gate": [vp, i32, i64, vp],
+        "qed_set_alloc_budget": [i64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -201,6 +203,12 @@ def digit_positions(model):
             pos += 1
     extra = list(range(pos, pos + model["n_extra"]))
     return photon, atom, extra
+
+
+def set_alloc_budget(nbytes):
+    """Test hook (qed_set_alloc_budget): the library's device allocations fail with
+    QED_ENOMEM once they would exceed `nbytes` in total; a negative value removes the limit."""
+    _check(lib().qed_set_alloc_budget(int(nbytes)), "qed_set_alloc_budget")
 
 
 def launch_count():
@@ -356,6 +364,12 @@ class Model:
         _check(lib().qed_autotune(self._h, int(steps), buf, 256, _stream_handle(stream)), "qed_autotune")
         return buf.value.decode()
 
+    def set_wait_gate(self, closed, budget_cycles=100000, stream=None):
+        """Test hook (qed_set_wait_gate): while closed, the split step's tensor-core kernels
+        time out on a bounded wait before doing any work, and sync() raises QED_ETIMEOUT."""
+        _check(lib().qed_set_wait_gate(self._h, 1 if closed else 0, int(budget_cycles), _stream_handle(stream)),
+               "qed_set_wait_gate")
+
     def set_scheme(self, scheme):
         """'lie' (first order) or 'strang' (second order: half Lindblad steps by the explicit
         midpoint rule around the unitary)."""
@@ -483,73 +497,6 @@ def select_states(model, rho0, steps_per_round, n_rounds, eps, stream=None):
     return reduced, out[:k * k].view(k, k).clone(), keep[:k].copy(), sizes
 
 
-def fit_final_populations(model, target, n_steps, names=("g",), precision="fp64", rho0=None, iters=60,
-                          step=1e-3, tol=1e-24, checkpoint_every=None):
-    """Fits couplings to measured final populations (point 4 of Sec. 2: choosing the model's
-    parameters to match data): least squares F(theta) = sum_k (p_k(theta) - target_k)^2 with
-    p = diag rho after n_steps, theta the couplings listed in `names` ("g", "zeta").  The
-    gradient comes from one qed_adjoint call with obs_diag = 2 (p - target), since
-    dF/dtheta = sum_k 2 (p_k - target_k) dp_k/dtheta; steepest descent with a step that
-    doubles after a success and halves after a failure.  `model` is a model dictionary;
-    target a length-D array.  Returns (fitted model dictionary, list of F per iteration)."""
-    import torch
-    m = dict(model)
-    tgt = torch.as_tensor(np.asarray(target, dtype=np.float64), device="cuda")
-    k = checkpoint_every or n_steps
-
-    def run(mm):
-        gm = Model(mm, precision=precision)
-        r0 = rho0
-        if r0 is None:
-            r0 = torch.zeros((gm.dim, gm.dim), dtype=torch.complex128, device="cuda")
-            i0 = gm.initial_index()
-            r0[i0, i0] = 1.0
-        rho = r0.clone()
-        gm.evolve(rho, n_steps)
-        gm.sync()
-        p = torch.real(torch.diagonal(rho)).contiguous()
-        return gm, r0, p, float(torch.sum((p - tgt) ** 2))
-
-    def theta(mm):
-        return np.concatenate([np.asarray(mm[n], dtype=np.float64) for n in names])
-
-    def with_theta(mm, th):
-        out, i = dict(mm), 0
-        for n in names:
-            c = len(mm[n])
-            out[n] = [float(x) for x in th[i:i + c]]
-            i += c
-        return out
-
-    gm, r0, p, F = run(m)
-    hist = [F]
-    for _ in range(iters):
-        if F <= tol:
-            break
-        _, gg, gz, _ = gm.adjoint(r0, n_steps, 2.0 * (p - tgt), checkpoint_every=k)
-        grads = {"g": gg.cpu().numpy(), "zeta": gz.cpu().numpy()}
-        gvec = np.concatenate([grads[n] for n in names])
-        gnorm = np.linalg.norm(gvec)
-        if not gnorm > 0:
-            break
-        th = theta(m)
-        while True:
-            trial = with_theta(m, th - step * gvec / gnorm)
-            gm2, r2, p2, F2 = run(trial)
-            if F2 < F:
-                m, gm, r0, p, F = trial, gm2, r2, p2, F2
-                step *= 2.0
-                break
-            gm2.close()
-            step *= 0.5
-            if step < 1e-15:
-                break
-        hist.append(F)
-        if step < 1e-15:
-            break
-    return m, hist
-
-
 def _check_rho(rho, dim):
     import torch
     if not isinstance(rho, torch.Tensor) or rho.dtype != torch.complex128 or not rho.is_cuda:
@@ -585,6 +532,12 @@ def _autograd_function():
             return grad_out * gg, grad_out * gz, grad_out * gj, None, None, None, None, None, None
 
     return QMELoss
+
+
+def fit_final_populations(*args, **kwargs):
+    """Least-squares fit of couplings to final populations (see fit.fit_final_populations)."""
+    from . import fit
+    return fit.fit_final_populations(*args, **kwargs)
 
 
 def qme_loss(g, zeta, gamma, model, rho0, n_steps, obs_diag, checkpoint_every=50, precision="fp64"):

@@ -64,7 +64,7 @@ inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 template <class T>
 qed_status up(T **dst, const std::vector<T> &v) {
     const size_t n = std::max<size_t>(v.size(), 1);
-    if (cudaMalloc((void **)dst, n * sizeof(T)) != cudaSuccess) {
+    if (device_malloc((void **)dst, n * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc failed for the adjoint tables");
         return QED_ENOMEM;
@@ -244,7 +244,7 @@ struct Buffers {
     }
     template <class T>
     qed_status get(T **p, size_t count) {
-        if (cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+        if (device_malloc((void **)p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed for the adjoint work space");
             return QED_ENOMEM;
@@ -410,7 +410,7 @@ qed_status make_twin(qed_model *m, cudaStream_t s) {
     t->prec = m->prec;
     t->renorm_every = 0;
     auto get = [&](void **p, size_t bytes) -> qed_status {
-        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        if (device_malloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed for the backward model");
             return QED_ENOMEM;
@@ -496,7 +496,14 @@ qed_status frechet_gradients(qed_model *m, Buffers &B, const double2 *Macc, doub
 // M = (sum_n rho_n lambda_n) U^+ is accumulated from one tensor-core product per step.
 qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, const double *obs_diag, double *loss,
                          double *grad_g, double *grad_zeta, double *grad_gamma, cudaStream_t s) {
-    ADJ_TRY(make_twin(m, s));
+    {
+        const qed_status st = make_twin(m, s);
+        if (st != QED_OK) {  // nothing half-built is kept for the next call
+            cudaStreamSynchronize(s);
+            adjoint_release(m);
+            return st;
+        }
+    }
     AdjointState &a = *m->adj;
     qed_model *t = a.twin;
     k = std::min<int64_t>(k, std::max<int64_t>(N, 1));
@@ -737,7 +744,14 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: the Strang step is differentiated on the FP64 path only");
         return QED_EUNSUPPORTED;
     }
-    ADJ_TRY(setup(m));
+    {
+        // a failed set-up (e.g. out of device memory) leaves no half-built tables behind
+        const qed_status st = setup(m);
+        if (st != QED_OK) {
+            adjoint_release(m);
+            return st;
+        }
+    }
     AdjointState &a = *m->adj;
     if ((a.n_g > 0 && !grad_g) || (a.n_zeta > 0 && !grad_zeta) || (a.n_jumps > 0 && !grad_gamma)) {
         set_error("qed_adjoint: gradient buffers missing");

@@ -1,6 +1,7 @@
 // The C ABI of libqed (declared in include/qed.h): argument checks, model lifetime,
 // the propagator stage and the step loop.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -18,6 +19,22 @@ static thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
 
 namespace {
+std::atomic<int64_t> g_alloc_budget{-1};  // bytes the library may still allocate (< 0: no limit)
+}
+
+cudaError_t device_malloc(void **p, size_t bytes) {
+    int64_t left = g_alloc_budget.load();
+    while (left >= 0) {
+        if ((int64_t)bytes > left) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_budget.compare_exchange_weak(left, left - (int64_t)bytes)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+namespace {
 
 qed_status einval(const std::string &msg) {
     set_error(msg);
@@ -28,7 +45,7 @@ template <class T>
 qed_status dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    cudaError_t e = device_malloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -50,7 +67,7 @@ void release(qed_model *m) {
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     void *ptrs[] = {m->U,      m->work1,   m->work2, m->work3,       m->phase,   m->anti, m->in_ptr,
                     m->in_jump, m->in_src, m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err,
-                    m->rho_int};
+                    m->rho_int, m->gate};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->err_host) cudaFreeHost(m->err_host);
@@ -264,6 +281,7 @@ qed_status build_device(qed_model *m, double dt, qed_precision prec, cudaStream_
     QED_TRY(dev_alloc(&m->work2, DD));
     QED_TRY(dev_alloc(&m->scalars, 16));
     QED_TRY(dev_alloc(&m->err, 1));
+    QED_TRY(dev_alloc(&m->gate, 1));
     QED_CUDA_TRY(cudaMallocHost((void **)&m->err_host, sizeof(uint32_t)));
     *m->err_host = 0;
     QED_CUDA_TRY(cudaMemset(m->err, 0, sizeof(uint32_t)));
@@ -458,6 +476,32 @@ qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choic
         std::strncpy(choice, c.c_str(), (size_t)choice_cap - 1);
         choice[choice_cap - 1] = 0;
     }
+    return QED_OK;
+}
+
+qed_status qed_set_wait_gate(qed_model *m, int32_t closed, int64_t budget_cycles, qed_stream stream) {
+    if (!m || budget_cycles < 0) return einval("qed_set_wait_gate: NULL model or negative budget");
+    if (m->prec == QED_FP64) {
+        set_error("qed_set_wait_gate: the FP64 path has no bounded waits");
+        return QED_EUNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t one = 1u;
+    QED_CUDA_TRY(cudaMemcpyAsync(m->gate, &one, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    m->gate_armed = closed != 0;
+    m->gate_budget = budget_cycles;
+    // the captured step graphs hold the old kernel parameters
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    for (auto &g : m->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return split_rebuild(m, s);
+}
+
+qed_status qed_set_alloc_budget(int64_t bytes) {
+    g_alloc_budget.store(bytes < 0 ? -1 : bytes);
     return QED_OK;
 }
 

@@ -12,7 +12,7 @@ namespace qed {
 namespace {
 
 qed_status alloc_work(double2 **p, size_t count) {
-    if (cudaMalloc((void **)p, count * sizeof(double2)) != cudaSuccess) {
+    if (device_malloc((void **)p, count * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc failed for the propagator work space");
         return QED_ENOMEM;

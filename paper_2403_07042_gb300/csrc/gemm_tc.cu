@@ -143,6 +143,8 @@ struct Params {
     uint32_t seg_a, seg_b;  // plane of segment q in bits 3q..3q+2 (kept in registers)
     int tx_bytes;   // bytes one stage receives
     int nseg;       // plane products
+    const uint32_t *gate;   // test hook: bounded wait for *gate == 0 before any load, or null
+    long long gate_budget;
     float *out;
     uint32_t *err;
     TcEpilogue epi;
@@ -512,9 +514,13 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmA) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tmB) : "memory");
     }
+    // the step's products keep two accumulators: columns [0, BN) for the leading plane
+    // product (hi x hi) and [BN, 2 BN) for the correction products, which are 2^-11 of it and
+    // would otherwise lose bits when added into the large partial sums
+    constexpr uint32_t kTmemCols = MODE == kEpiPlain ? BN : 2 * BN;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTcBN)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -525,6 +531,21 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     // operands and outputs are shared with the neighbouring kernels of the step
     pdl_wait();
     pdl_trigger();
+    if (p.gate) {
+        // wait-gate test hook: a bounded wait on a flag, taken before this CTA issues any
+        // load or product; when it runs out the CTA records the timeout and does no work
+        if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            while (*(volatile const uint32_t *)p.gate != 0u) {
+                if (clock64() - t0 > p.gate_budget) {
+                    *abort_flag = 1;
+                    atomicOr(p.err, kErrTimeout);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+    }
 
     constexpr int rows = kTcBM / S;
     const int r0 = split * rows;
@@ -570,9 +591,10 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
         // MMA issuer
         constexpr uint32_t idesc = idesc_f16(kTcBM, kTcBN);
         for (int i = 0; i < nkb; ++i) {
+            if (*abort_flag) break;  // the stages already issued are drained at the end
             const int s = i % kTcStages;
             const uint32_t par = (i / kTcStages) & 1;
-            const long long budget = *abort_flag ? 2000000LL : kWaitCycles;
+            const long long budget = kWaitCycles;
             if (!mbar_wait(full0 + 8 * s, par, budget)) {
                 *abort_flag = 1;
                 atomicOr(p.err, kErrTimeout);
@@ -593,9 +615,11 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
                         const int pa = (p.seg_a >> (3 * q)) & 7, pb = (p.seg_b >> (3 * q)) & 7;
                         const uint64_t ad = smem_desc_sw128(smem_u32(st + pa * kStageA));
                         const uint64_t bd = smem_desc_sw128(smem_u32(st + NA * kStageA + pb * kTileB));
+                        const uint32_t acc = q == 0 ? tmem : tmem + (uint32_t)BN;
+                        const bool first = i == 0 && q <= 1;  // first product into its accumulator
 #pragma unroll
                         for (int k = 0; k < kTcBK / 16; ++k)
-                            mma_f16(tmem, ad + 2 * k, bd + 2 * k, idesc, (i > 0 || q > 0 || k > 0) ? 1u : 0u);
+                            mma_f16(acc, ad + 2 * k, bd + 2 * k, idesc, (first && k == 0) ? 0u : 1u);
                     }
                 }
             }
@@ -654,22 +678,17 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
         float *tile = (float *)ring;
         if (ok) {
             const int c0 = (warp >> 2) * cols;
+            const bool corr = p.nseg > 1;
 #pragma unroll 1
-            for (int c = c0; c < c0 + cols; c += 64) {
-                uint32_t r0v[32], r1v[32];
-                tmem_ld32_async(tm_row + (uint32_t)c, r0v);
-                tmem_ld32_async(tm_row + (uint32_t)(c + 32), r1v);
+            for (int c = c0; c < c0 + cols; c += 32) {
+                uint32_t mv[32], cv[32];
+                tmem_ld32_async(tm_row + (uint32_t)c, mv);
+                tmem_ld32_async(tm_row + (uint32_t)(BN + c), cv);
                 tmem_wait();
                 float *dst = tile + ((warp & 3) * 32 + lane) * TS + c;
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    *(float4 *)(dst + 4 * q) = make_float4(__uint_as_float(r0v[4 * q]), __uint_as_float(r0v[4 * q + 1]),
-                                                           __uint_as_float(r0v[4 * q + 2]), __uint_as_float(r0v[4 * q + 3]));
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    *(float4 *)(dst + 32 + 4 * q) =
-                        make_float4(__uint_as_float(r1v[4 * q]), __uint_as_float(r1v[4 * q + 1]),
-                                    __uint_as_float(r1v[4 * q + 2]), __uint_as_float(r1v[4 * q + 3]));
+                for (int q = 0; q < 32; ++q)
+                    dst[q] = __uint_as_float(mv[q]) + (corr ? __uint_as_float(cv[q]) : 0.f);
             }
         }
         if constexpr (MODE == kEpiV) {
@@ -700,7 +719,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     }
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
@@ -719,6 +738,8 @@ Params params_of(const GemmJob &jb, const TcSegs &segs, uint32_t *err) {
     p.kb_per_split = jb.kb_per_split;
     p.tx_bytes = jb.tx_bytes;
     p.nseg = segs.nseg;
+    p.gate = jb.gate;
+    p.gate_budget = jb.gate_budget;
     p.epi = jb.epi;
     p.seg_a = 0;
     p.seg_b = 0;
@@ -747,6 +768,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tc_gemm_grouped_kernel(con
     p.kb_per_split = jb.kb_per_split;
     p.tx_bytes = jb.tx_bytes;
     p.nseg = segs.nseg;
+    p.gate = jb.gate;
+    p.gate_budget = jb.gate_budget;
     p.epi = jb.epi;
     p.seg_a = 0;
     p.seg_b = 0;
@@ -1020,6 +1043,8 @@ cudaError_t tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStrea
     p.kb_per_split = g.kb_per_split;
     p.tx_bytes = (int)kStageA + g.b_box_rows * kTcBK * 2;
     p.nseg = g.nseg;
+    p.gate = nullptr;
+    p.gate_budget = 0;
     p.epi = TcEpilogue();
     p.out = out;
     p.err = err;
@@ -1049,7 +1074,7 @@ extern "C" qed_status qed_tc_gemm(const void *a_planes, int32_t planes_a, const 
         return QED_EINVAL;
     }
     uint32_t *err = nullptr;
-    if (cudaMalloc((void **)&err, 4) != cudaSuccess) {
+    if (device_malloc((void **)&err, 4) != cudaSuccess) {
         cudaGetLastError();
         set_error("qed_tc_gemm: cudaMalloc failed");
         return QED_ENOMEM;

@@ -91,6 +91,8 @@ struct GemmJob {
     int M, N, kb_per_seg, kb_per_split;
     int tx_bytes;              // bytes one stage receives (A tile + B box)
     int mode;                  // kEpiPlain, kEpiW or kEpiV
+    const uint32_t *gate;      // test hook (qed_set_wait_gate): wait for *gate == 0, or null
+    long long gate_budget;     // cycles that wait may take before the CTA gives up
     TcEpilogue epi;
 };
 

@@ -16,6 +16,10 @@ namespace qed {
 
 void set_error(const std::string &msg);
 
+// Every device allocation of the library goes through here (cudaMalloc), so that the
+// allocation-failure hook (qed_set_alloc_budget) can make it fail like an exhausted device.
+cudaError_t device_malloc(void **p, size_t bytes);
+
 #define QED_CUDA_TRY(call)                                                        \
     do {                                                                          \
         cudaError_t e_ = (call);                                                  \
@@ -75,6 +79,11 @@ struct qed_model {
     double *scalars = nullptr;        // device scratch: trace etc.
     uint32_t *err = nullptr;          // device error word
     uint32_t *err_host = nullptr;     // pinned mirror
+    // wait-gate test hook (qed_set_wait_gate): while armed, the split step's tensor-core
+    // kernels wait up to gate_budget cycles for *gate to become 0, which nothing does
+    uint32_t *gate = nullptr;
+    bool gate_armed = false;
+    int64_t gate_budget = 0;
 
     qed::SplitState *sp = nullptr;
     qed::AdjointState *adj = nullptr;

@@ -558,7 +558,7 @@ double pow2_scale(double maxabs, int target_exp) {
 
 template <class T>
 qed_status alloc(T **p, size_t count) {
-    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    if (device_malloc((void **)p, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc failed for the split-precision buffers");
         return QED_ENOMEM;
@@ -653,6 +653,8 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
             j.kb_per_seg = g.K / kTcBK;
             j.kb_per_split = g.kb_per_split;
             j.out = nullptr;
+            j.gate = m->gate_armed ? m->gate : nullptr;
+            j.gate_budget = m->gate_budget;
             j.mode = q == 0 ? kEpiW : kEpiV;
             j.tx_bytes = tc_stage_tx_bytes(g, j.mode);
             j.epi = TcEpilogue();
@@ -974,6 +976,12 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
              std::to_string(g2.bn) + "-wide x" + std::to_string(g2.splits) + " slices, " +
              std::to_string(1e3 * best / steps) + " us per step";
     return QED_OK;
+}
+
+qed_status split_rebuild(qed_model *m, cudaStream_t s) {
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    qed_model *self[1] = {m};
+    return build_batch(m->sp->self, self, 1, true);
 }
 
 void split_set_scheme(qed_model *m, int scheme) {

@@ -17,6 +17,8 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s);  // ca
 void split_check_density(qed_model *m, const double2 *rho, cudaStream_t s);
 void split_step(qed_model *m, cudaStream_t s);
 void split_set_scheme(qed_model *m, int scheme);  // QED_SCHEME_LIE or QED_SCHEME_STRANG
+// Rebuilds the model's step tables (after a change of its wait-gate hook); synchronises `s`.
+qed_status split_rebuild(qed_model *m, cudaStream_t s);
 // Times whole steps over the tile widths and split-K factors of both products and keeps
 // the fastest; `choice` describes it.
 qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &choice);
