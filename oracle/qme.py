@@ -26,6 +26,9 @@ quantum electrodynamics applications"):
   g (a sigma^+ + a^+ sigma)), the hopping term of Eq. (12) (zeta (a_i^+ a_j + a_i a_j^+) on
   each nearest-neighbour pair once) and a transverse term zeta sigma_x on extra
   two-level digits (the tunnelling of Eq. 4 written in its eigenbasis-free form).
+* two further step schemes built from the same two stages: the symmetric (Strang) step,
+  and the effective-Hamiltonian form of Eq. (3) regrouped (U_eff = exp(-i dt (H - i/2
+  sum gamma A^+A)) carries the anticommutator, one Euler step adds the jump terms).
 * discrete adjoint gradients of tr(O rho_N) with respect to g, zeta and gamma.
 
 Every function below is pinned by tests that do not re-derive it: closed forms (Rabi
@@ -386,7 +389,29 @@ def step_strang(rho, U, jumps, dt):
     return lindblad_midpoint(V, jumps, 0.5 * dt)
 
 
-STEPS = {"lie": step, "strang": step_strang}
+def effective_propagator(H, jumps, dt):
+    """U_eff = exp(-i dt H_eff), H_eff = H - (i/2) sum_j gamma_j A_j^+ A_j: the anticommutator
+    of Eq. (3) folded into a non-Hermitian generator together with the commutator of Eq. (2).
+    H_eff is not Hermitian, so the exponential is scipy's expm (not an eigendecomposition)."""
+    K = np.zeros_like(H, dtype=np.complex128)
+    for gamma, A in jumps:
+        K += gamma * _dense(A.conj().T @ A)
+    return sla.expm(-1j * dt * (np.asarray(H, dtype=np.complex128) - 0.5j * K))
+
+
+def step_effective(rho, U, jumps, dt):
+    """One step of Eq. (3) regrouped: V = U_eff rho U_eff^+ carries the Hamiltonian and the
+    anticommutator part exactly (U is the effective propagator), then one Euler step of the
+    jump terms, V + dt sum_j gamma_j A_j V A_j^+.  First order in dt, completely positive,
+    trace kept to O(dt^2) per step."""
+    V = U @ rho @ U.conj().T
+    out = V.copy()
+    for gamma, A in jumps:
+        _add_sandwich(out, dt * gamma, A, V)
+    return out
+
+
+STEPS = {"lie": step, "strang": step_strang, "effective": step_effective}
 
 
 def observable_weights(model, basis):
@@ -413,14 +438,15 @@ def observables(rho, weights, obs_ids):
 
 def evolve(model, rho0=None, n_steps=None, record_every=None, obs_ids=None, U=None,
            basis=None, return_records=True, scheme="lie"):
-    """Integrate n_steps with the step of `scheme` ('lie' or 'strang'); record observables
-    at steps 0, r, 2r, ... (<= n_steps)."""
+    """Integrate n_steps with the step of `scheme` ('lie', 'strang' or 'effective', whose U
+    is the effective propagator); record observables at steps 0, r, 2r, ... (<= n_steps)."""
     advance = STEPS[scheme]
     basis = basis or enumerate_basis(model)
     H = hamiltonian(model, basis)
     dt = model["dt"]
-    U = propagator(H, dt) if U is None else U
     jumps = jump_operators(model, basis)
+    if U is None:
+        U = effective_propagator(H, jumps, dt) if scheme == "effective" else propagator(H, dt)
     rho = initial_density(model, basis) if rho0 is None else np.array(rho0, dtype=np.complex128)
     n_steps = model["n_steps"] if n_steps is None else n_steps
     r = record_every or model["record_every"]

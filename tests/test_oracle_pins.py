@@ -476,6 +476,80 @@ def test_strang_trace_and_unitary_limit():
     assert np.abs(rho_u - Un @ rho0 @ Un.conj().T).max() < 1e-12
 
 
+# ---------------------------------------------------------------- effective-Hamiltonian scheme
+def _photon_cavity(gamma, dt, steps, n_max=2, n0=2):
+    return W._model(n_cavities=1, atoms_per_cavity=[0], n_max=[n_max], jumps=[(0, 0, gamma)], dt=dt,
+                    n_steps=steps, init={"photons": {0: n0}})
+
+
+def test_effective_propagator_closed_form():
+    """H = omega a^+a, A = a: H_eff = (omega - i gamma/2) a^+a is diagonal, so
+    U_eff = diag(exp(-i omega k dt - gamma k dt / 2))."""
+    gamma, dt = 0.03, 0.1
+    m = _photon_cavity(gamma, dt, 1, n_max=4)
+    b = oracle.enumerate_basis(m)
+    U = oracle.effective_propagator(oracle.hamiltonian(m, b), oracle.jump_operators(m, b), dt)
+    k = np.arange(5)
+    assert np.abs(U - np.diag(np.exp(-1j * 1.0 * k * dt - 0.5 * gamma * k * dt))).max() < 1e-15
+
+
+def test_effective_discrete_photon_decay():
+    """Two photons, H = omega a^+a, A = a.  V_kk = exp(-gamma k dt) p_k, and the jump term
+    adds dt gamma (k+1) V_{k+1,k+1} to p_k, so the populations follow
+        p2' = e^{-2 gamma dt} p2,   p1' = e^{-gamma dt} p1 + 2 gamma dt e^{-2 gamma dt} p2,
+        p0' = p0 + gamma dt e^{-gamma dt} p1;
+    in particular p2 decays exactly as exp(-2 gamma t)."""
+    gamma, dt, steps = 0.02, 0.1, 400
+    m = _photon_cavity(gamma, dt, steps)
+    b = oracle.enumerate_basis(m)
+    _, rec = oracle.evolve(m, basis=b, obs_ids=[0, 1, 2], scheme="effective", record_every=1)
+    p = np.array([0.0, 0.0, 1.0])
+    want = [p.copy()]
+    a1, a2 = np.exp(-gamma * dt), np.exp(-2 * gamma * dt)
+    for _ in range(steps):
+        p = np.array([p[0] + gamma * dt * a1 * p[1], a1 * p[1] + 2 * gamma * dt * a2 * p[2], a2 * p[2]])
+        want.append(p.copy())
+    # rounding only: a few units of 2^-53 per step over 400 steps
+    assert np.abs(rec - np.array(want)).max() < 400 * 8 * 2.0 ** -53
+    assert abs(rec[-1, 2] - np.exp(-2 * gamma * dt * steps)) < 400 * 8 * 2.0 ** -53
+
+
+def test_effective_first_order_convergence_to_continuum():
+    """The scheme converges to exp(L t) rho_0 at first order: halving dt halves the error."""
+    m = W.jch_two_cavities(gamma=0.05)
+    b = oracle.enumerate_basis(m)
+    t = 20.0
+    exact = oracle.continuum(m, t, basis=b)
+    errs = []
+    for dt in (0.2, 0.1, 0.05):
+        mm = dict(m, dt=dt, n_steps=int(round(t / dt)))
+        rho = oracle.evolve(mm, basis=b, return_records=False, scheme="effective")
+        errs.append(np.abs(rho - exact).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 1.8 <= e1 / e2 <= 2.2, errs
+
+
+def test_effective_positivity_trace_and_unitary_limit():
+    """Each step is a sum of completely positive maps (U_eff . U_eff^+ and the jump
+    sandwiches), so rho stays positive; the trace drifts by O(dt^2) per step (halving dt over
+    a fixed time halves the drift); without jumps the step is U rho U^+."""
+    m = W.hb_shaped(n_steps=200, record_every=50)
+    m.update(n_cavities=1, atoms_per_cavity=[2], n_max=[2], g=m["g"][:2], jumps=[(0, 0, 0.05), (2, 0, 0.02)])
+    b = oracle.enumerate_basis(m)
+    rho0 = W.random_density(b.dim, seed=8)
+    drift = []
+    for dt, n in ((0.1, 200), (0.05, 400)):
+        rho = oracle.evolve(dict(m, dt=dt), rho0=rho0, n_steps=n, basis=b, return_records=False, scheme="effective")
+        assert np.linalg.eigvalsh(0.5 * (rho + rho.conj().T)).min() > -1e-13
+        drift.append(abs(np.trace(rho).real - 1.0))
+    assert 1.8 <= drift[0] / drift[1] <= 2.2, drift
+    m0 = dict(m, jumps=[])
+    U = oracle.propagator(oracle.hamiltonian(m0, b), m0["dt"])
+    rho_u = oracle.evolve(m0, rho0=rho0, n_steps=100, basis=b, return_records=False, scheme="effective")
+    Un = np.linalg.matrix_power(U, 100)
+    assert np.abs(rho_u - Un @ rho0 @ Un.conj().T).max() < 1e-12
+
+
 # ---------------------------------------------------------------- state selection (Sec. 3.2)
 def test_selection_with_eps_zero_keeps_every_state_and_the_trajectory():
     """eps = 0 deletes nothing: the rounds reproduce the plain trajectory (each round's
