@@ -59,8 +59,13 @@ typedef enum {
  * the Lindblad term of Eq. 3; the paper does not state how they are combined). */
 enum {
     QED_SCHEME_LIE = 0,    /* rho <- E(dt) U rho U^+, E(t) one explicit Euler step: first order */
-    QED_SCHEME_STRANG = 1  /* rho <- E2(dt/2) U E2(dt/2)(rho) U^+, E2(t) X = X + t L(X + t/2 L(X))
+    QED_SCHEME_STRANG = 1, /* rho <- E2(dt/2) U E2(dt/2)(rho) U^+, E2(t) X = X + t L(X + t/2 L(X))
                               (explicit midpoint rule): second order in dt                   */
+    QED_SCHEME_EFFECTIVE = 2 /* Eq. 3 regrouped: V = U_eff rho U_eff^+ with
+                              U_eff = exp(-i dt (H - i/2 sum_j gamma_j A_j^+ A_j)) (the
+                              anticommutator inside the propagator), then
+                              rho <- V + dt sum_j gamma_j A_j V A_j^+: first order, completely
+                              positive, trace kept to O(dt^2) per step                       */
 };
 
 /* Basis kinds (Sec. 4.2, Eqs. 10-11 restrict the 2^Area product space to one photon). */
@@ -167,11 +172,18 @@ qed_status qed_n_observables(const qed_model *m, int32_t *n);
  * (0 = never; default 100).  Ignored in FP64. */
 qed_status qed_set_renorm_every(qed_model *m, int32_t every);
 
-/* The time-stepping scheme (QED_SCHEME_LIE, the default, or QED_SCHEME_STRANG) that
- * qed_evolve and qed_evolve_batched use from now on; the Strang scheme runs four Lindblad
- * stages per step instead of one.  EINVAL for an unknown scheme; ENOMEM if the FP64 path's
- * stage buffer cannot be allocated.  Synchronises the device.  qed_adjoint differentiates
- * the Strang step on the FP64 path (EUNSUPPORTED in split precision). */
+/* The time-stepping scheme (QED_SCHEME_LIE, the default, QED_SCHEME_STRANG or
+ * QED_SCHEME_EFFECTIVE) that qed_evolve and qed_evolve_batched use from now on; the Strang
+ * scheme runs four Lindblad stages per step instead of one.  Switching to or from the
+ * effective scheme recomputes the propagator (U_eff = exp(X), X = -i dt H - (dt/2) diag(d),
+ * d_k = sum_j gamma_j (A_j^+ A_j)_kk, by Pade-13 scaling and squaring; every jump operator
+ * here is a monomial, so A_j^+ A_j is diagonal) and, in split precision, the increment form
+ * with the damped phases P_k = exp(-i H_kk dt - d_k dt/2); under that scheme the split
+ * path's periodic pass symmetrises rho without dividing by its trace (the scheme's own
+ * trace drift is part of its result).  EINVAL for an unknown scheme; ENOMEM if a buffer
+ * cannot be allocated; ENUMERIC for a singular Pade denominator.  Synchronises the device.
+ * qed_adjoint differentiates the Strang step on the FP64 path (EUNSUPPORTED in split
+ * precision) and does not differentiate the effective step (EUNSUPPORTED). */
 qed_status qed_set_scheme(qed_model *m, int32_t scheme);
 
 /* Tile autotuner (the paper has no counterpart: it concerns only how this library maps the
@@ -199,7 +211,8 @@ qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choic
  * trace at a renormalisation) surface through qed_sync_status.
  *
  * Split precision (QED_SPLIT_FP16x2) accepts only a density matrix: rho Hermitian and of
- * unit trace (|rho_mn - conj(rho_nm)| <= 1e-8 and |tr rho - 1| <= 1e-6).  Its first product
+ * unit trace (|rho_mn - conj(rho_nm)| <= 1e-8 and |tr rho - 1| <= 1e-6; under
+ * QED_SCHEME_EFFECTIVE, whose own steps move the trace, 0 < tr rho <= 1 + 1e-6).  Its first product
  * reads the row-major rho as rho^T = conj(rho), the second forms the Hermitian X = W Delta^+,
  * the FP16 scale assumes |rho_mn| <= 1 and the renormalisation divides by tr rho; any other
  * input would give a silently different answer.  A device check at the start of the call

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libqed.so")
 QED_OK, QED_EINVAL, QED_ENOMEM, QED_ECUDA, QED_ETIMEOUT, QED_ENUMERIC, QED_EUNSUPPORTED = range(7)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "ENUMERIC", "EUNSUPPORTED"]
 PRECISIONS = {"fp64": 0, "split_fp16x2": 1, "split_bf16x3": 2, "split_tf32x3": 3}
-SCHEMES = {"lie": 0, "strang": 1}
+SCHEMES = {"lie": 0, "strang": 1, "effective": 2}
 
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -371,8 +371,9 @@ class Model:
                "qed_set_wait_gate")
 
     def set_scheme(self, scheme):
-        """'lie' (first order) or 'strang' (second order: half Lindblad steps by the explicit
-        midpoint rule around the unitary)."""
+        """'lie' (first order), 'strang' (second order: half Lindblad steps by the explicit
+        midpoint rule around the unitary) or 'effective' (the anticommutator inside a
+        non-unitary propagator, then the jump terms)."""
         _check(lib().qed_set_scheme(self._h, SCHEMES[scheme]), "qed_set_scheme")
         self.scheme = scheme
 

@@ -740,6 +740,10 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: n_steps >= 0 and checkpoint_every > 0 required");
         return QED_EINVAL;
     }
+    if (m->scheme == QED_SCHEME_EFFECTIVE) {
+        set_error("qed_adjoint: the effective-Hamiltonian step is not differentiated");
+        return QED_EUNSUPPORTED;
+    }
     if (m->scheme != QED_SCHEME_LIE && m->prec != QED_FP64) {
         set_error("qed_adjoint: the Strang step is differentiated on the FP64 path only");
         return QED_EUNSUPPORTED;

@@ -67,7 +67,7 @@ void release(qed_model *m) {
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     void *ptrs[] = {m->U,      m->work1,   m->work2, m->work3,       m->phase,   m->anti, m->in_ptr,
                     m->in_jump, m->in_src, m->in_coef, m->obs_w, m->obs_ids_dev, m->scalars, m->err,
-                    m->rho_int, m->gate};
+                    m->rho_int, m->gate, m->anti_zero};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (m->err_host) cudaFreeHost(m->err_host);
@@ -128,15 +128,7 @@ qed_status upload_tables(qed_model *m) {
     }
     QED_TRY(dev_alloc(&m->obs_w, w.size()));
     QED_CUDA_TRY(cudaMemcpy(m->obs_w, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
-    // phases P_k = exp(-i H_kk dt)
-    std::vector<double2> ph((size_t)D);
-    std::vector<double> diag((size_t)D, 0.0);
-    for (const auto &e : hm.h_entries)
-        if (e.row == e.col) diag[(size_t)e.row] += entry_coefficient(hm, e) * e.unit;
-    for (int64_t k = 0; k < D; ++k)
-        ph[(size_t)k] = make_double2(std::cos(diag[(size_t)k] * m->dt), -std::sin(diag[(size_t)k] * m->dt));
-    QED_TRY(dev_alloc(&m->phase, (size_t)D));
-    QED_CUDA_TRY(cudaMemcpy(m->phase, ph.data(), (size_t)D * 16, cudaMemcpyHostToDevice));
+    QED_TRY(dev_alloc(&m->phase, (size_t)D));  // values: compute_propagator
     return QED_OK;
 }
 
@@ -168,13 +160,15 @@ int step_f64(qed_model *m, double2 *rho, cudaStream_t s, cudaEvent_t *ev = nullp
     const int64_t D = m->D;
     const double dt = m->dt;
     const bool strang = m->scheme == QED_SCHEME_STRANG;
+    // the effective-Hamiltonian step: U is U_eff and the anticommutator is inside it
+    const double *anti = m->scheme == QED_SCHEME_EFFECTIVE ? m->anti_zero : m->anti;
     int e = 0;
     auto mark = [&]() {
         if (ev) cudaEventRecord(ev[e], s);
         ++e;
     };
     auto stage = [&](const double2 *X, const double2 *B, double2 *out, double tau) {
-        lindblad_axpy_f64(s, D, X, B, out, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, tau);
+        lindblad_axpy_f64(s, D, X, B, out, anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, tau);
     };
     if (strang) {
         mark();
@@ -192,7 +186,7 @@ int step_f64(qed_model *m, double2 *rho, cudaStream_t s, cudaEvent_t *ev = nullp
         mark();
         stage(m->work3, m->work2, rho, 0.5 * dt);
     } else {
-        dissipate_f64(s, D, m->work2, rho, m->anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, dt);
+        dissipate_f64(s, D, m->work2, rho, anti, m->in_ptr, m->in_jump, m->in_src, m->in_coef, dt);
     }
     mark();
     if (label)
@@ -268,6 +262,53 @@ int64_t next_multiple_after(int64_t off, int64_t i, int64_t every) {
     return i + (every - (off + i) % every);
 }
 
+// The propagator of a scheme into m->U and the diagonal phases into m->phase ("Taylor
+// approximation" stage, Sec. 4.2): for the Lie and Strang steps U = exp(-i H dt) (Pade-13 on
+// the Hermitian H) and P_k = exp(-i H_kk dt); for the effective-Hamiltonian step
+// U = exp(X), X = -i dt H - (dt/2) diag(d) with d_k = sum_j gamma_j (A_j^+ A_j)_kk (every
+// jump operator of this library is a monomial, so A_j^+ A_j is diagonal), and
+// P_k = exp(-i H_kk dt - d_k dt/2).  Synchronises `s`.
+qed_status compute_propagator(qed_model *m, int scheme, cudaStream_t s) {
+    const int64_t D = m->D;
+    const double dt = m->dt;
+    const HostModel &hm = m->host;
+    const bool eff = scheme == QED_SCHEME_EFFECTIVE;
+    std::vector<cplx> Hd;
+    dense_hamiltonian(hm, Hd);
+    if (eff)
+        for (int64_t k = 0; k < D; ++k) {
+            // X = -i dt H - (dt/2) diag(d), stored in place of H
+            for (int64_t l = 0; l < D; ++l) Hd[(size_t)(k * D + l)] *= cplx(0.0, -dt);
+            Hd[(size_t)(k * D + k)] -= 0.5 * dt * hm.anti_diag[(size_t)k];
+        }
+    double norm1 = 0.0;
+    for (int64_t c = 0; c < D; ++c) {
+        double col = 0.0;
+        for (int64_t r = 0; r < D; ++r) col += std::abs(Hd[(size_t)(r * D + c)]);
+        norm1 = std::max(norm1, col);
+    }
+    QED_CUDA_TRY(cudaMemcpyAsync(m->work1, Hd.data(), (size_t)(D * D) * 16, cudaMemcpyHostToDevice, s));
+    if (eff)
+        QED_TRY(expm_pade13(s, D, m->work1, norm1, m->U, m->err));
+    else
+        QED_TRY(propagator(s, D, dt, m->work1, norm1, m->U, m->err));
+    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
+    if (*m->err_host & kErrSingular) {
+        set_error("singular Pade denominator");
+        return QED_ENUMERIC;
+    }
+    std::vector<double> diag((size_t)D, 0.0);
+    for (const auto &e : hm.h_entries)
+        if (e.row == e.col) diag[(size_t)e.row] += entry_coefficient(hm, e) * e.unit;
+    std::vector<double2> ph((size_t)D);
+    for (int64_t k = 0; k < D; ++k) {
+        const double amp = eff ? std::exp(-0.5 * dt * hm.anti_diag[(size_t)k]) : 1.0;
+        ph[(size_t)k] = make_double2(amp * std::cos(diag[(size_t)k] * dt), -amp * std::sin(diag[(size_t)k] * dt));
+    }
+    QED_CUDA_TRY(cudaMemcpy(m->phase, ph.data(), (size_t)D * 16, cudaMemcpyHostToDevice));
+    return QED_OK;
+}
+
 // Device side of a model whose host model m->host is built: operators, tables, U, and
 // the split-precision state.  Synchronises `s`.
 qed_status build_device(qed_model *m, double dt, qed_precision prec, cudaStream_t s) {
@@ -287,22 +328,7 @@ qed_status build_device(qed_model *m, double dt, qed_precision prec, cudaStream_
     QED_CUDA_TRY(cudaMemset(m->err, 0, sizeof(uint32_t)));
     QED_TRY(upload_tables(m));
     for (auto &e : m->ev) QED_CUDA_TRY(cudaEventCreate(&e));
-    // H into work1, then U = exp(-i H dt)
-    std::vector<cplx> Hd;
-    dense_hamiltonian(m->host, Hd);
-    double norm1 = 0.0;
-    for (int64_t c = 0; c < D; ++c) {
-        double col = 0.0;
-        for (int64_t r = 0; r < D; ++r) col += std::abs(Hd[(size_t)(r * D + c)]);
-        norm1 = std::max(norm1, col);
-    }
-    QED_CUDA_TRY(cudaMemcpyAsync(m->work1, Hd.data(), DD * 16, cudaMemcpyHostToDevice, s));
-    QED_TRY(propagator(s, D, dt, m->work1, norm1, m->U, m->err));
-    QED_CUDA_TRY(cudaMemcpy(m->err_host, m->err, 4, cudaMemcpyDeviceToHost));
-    if (*m->err_host & kErrSingular) {
-        set_error("singular Pade denominator");
-        return QED_ENUMERIC;
-    }
+    QED_TRY(compute_propagator(m, QED_SCHEME_LIE, s));
     if (prec != QED_FP64) QED_TRY(split_prepare(m, s));
     QED_CUDA_TRY(cudaStreamSynchronize(s));
     return QED_OK;
@@ -506,10 +532,15 @@ qed_status qed_set_alloc_budget(int64_t bytes) {
 }
 
 qed_status qed_set_scheme(qed_model *m, int32_t scheme) {
-    if (!m || (scheme != QED_SCHEME_LIE && scheme != QED_SCHEME_STRANG)) return einval("bad scheme");
+    if (!m || (scheme != QED_SCHEME_LIE && scheme != QED_SCHEME_STRANG && scheme != QED_SCHEME_EFFECTIVE))
+        return einval("bad scheme");
     if (scheme == m->scheme) return QED_OK;
     if (scheme == QED_SCHEME_STRANG && m->prec == QED_FP64 && !m->work3)
         QED_TRY(dev_alloc(&m->work3, (size_t)(m->D * m->D)));
+    if (scheme == QED_SCHEME_EFFECTIVE && !m->anti_zero) {
+        QED_TRY(dev_alloc(&m->anti_zero, (size_t)m->D));
+        QED_CUDA_TRY(cudaMemset(m->anti_zero, 0, (size_t)m->D * sizeof(double)));
+    }
     // the captured step graphs belong to the old scheme
     QED_CUDA_TRY(cudaDeviceSynchronize());
     for (auto &g : m->graph)
@@ -517,8 +548,15 @@ qed_status qed_set_scheme(qed_model *m, int32_t scheme) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    const bool new_u = (scheme == QED_SCHEME_EFFECTIVE) != (m->scheme == QED_SCHEME_EFFECTIVE);
     m->scheme = scheme;
+    if (new_u) {
+        // the effective step has its own propagator, phases and (no) damping table
+        QED_TRY(compute_propagator(m, scheme, nullptr));
+        if (m->prec != QED_FP64) QED_TRY(split_prepare(m, nullptr));
+    }
     split_set_scheme(m, scheme);
+    QED_CUDA_TRY(cudaDeviceSynchronize());
     return QED_OK;
 }
 

@@ -64,6 +64,7 @@ struct qed_model {
     double2 *work3 = nullptr;    // D x D stage buffer of the Strang step (FP64 path, on demand)
     double2 *phase = nullptr;    // D: P_k = exp(-i H_kk dt)
     double *anti = nullptr;      // D: d_k = sum_j gamma_j (A_j^+A_j)_kk
+    double *anti_zero = nullptr; // D zeros: the damping table of the effective-Hamiltonian step
     // incoming jump lists per row m, sorted by jump id: entries [in_ptr[m], in_ptr[m+1])
     int32_t *in_ptr = nullptr;   // D + 1
     int32_t *in_jump = nullptr;

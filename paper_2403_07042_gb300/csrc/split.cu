@@ -119,13 +119,19 @@ __device__ __forceinline__ void split_half3(double x, __half &hi, __half &mid, _
     lo = __double2half(r - (double)__half2float(mid));
 }
 
-// Delta = conj(P_k) U_kl - delta_kl   (|P_k| = 1, so P^-1 = conj(P))
-__global__ void make_delta_kernel(int64_t D, const double2 *U, const double2 *P, double2 *Dl) {
+// Delta = P_k^-1 U_kl - delta_kl: conj(P_k) U_kl for the unit phases of U = exp(-i H dt)
+// (unit != 0), conj(P_k) U_kl / |P_k|^2 for the damped phases of the effective step
+__global__ void make_delta_kernel(int64_t D, const double2 *U, const double2 *P, double2 *Dl, int unit) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= D * D) return;
     int64_t k = idx / D, l = idx % D;
     double2 u = U[idx], p = P[k];
     double2 d = make_double2(p.x * u.x + p.y * u.y, p.x * u.y - p.y * u.x);
+    if (!unit) {
+        const double inv = 1.0 / (p.x * p.x + p.y * p.y);
+        d.x *= inv;
+        d.y *= inv;
+    }
     if (k == l) d.x -= 1.0;
     Dl[idx] = d;
 }
@@ -211,7 +217,8 @@ __global__ void planes_from_state_kernel(int64_t D, int64_t Dp, const float4 *st
 // row-major rho read as rho^T = conj(rho), and X = W Delta^+ is formed as a Hermitian
 // matrix) and of unit trace (the FP16 scale assumes |rho_mn| <= 1 and the renormalisation
 // divides by the trace).  One thread per pair m <= n; block 0 also sums the diagonal.
-__global__ void __launch_bounds__(256) check_density_kernel(int64_t D, const double2 *rho, uint32_t *err) {
+__global__ void __launch_bounds__(256) check_density_kernel(int64_t D, const double2 *rho, uint32_t *err,
+                                                             int unit_trace) {
     __shared__ double part[256];
     const int t = threadIdx.y * 32 + threadIdx.x;
     const int64_t n = (int64_t)blockIdx.x * 32 + threadIdx.x;
@@ -230,7 +237,9 @@ __global__ void __launch_bounds__(256) check_density_kernel(int64_t D, const dou
         if (t < h) part[t] += part[t + h];
         __syncthreads();
     }
-    if (t == 0 && !(fabs(part[0] - 1.0) <= kDensityTraceTol)) atomicOr(err, kErrNotDensity);
+    const bool trace_ok = unit_trace ? fabs(part[0] - 1.0) <= kDensityTraceTol
+                                     : (part[0] > 0.0 && part[0] <= 1.0 + kDensityTraceTol);
+    if (t == 0 && !trace_ok) atomicOr(err, kErrNotDensity);
 }
 
 __global__ void export_kernel(int64_t D, const float4 *st, double2 *rho) {
@@ -518,15 +527,16 @@ __global__ void __launch_bounds__(1024) trace_df_kernel(int64_t D, const float4 
     }
 }
 
-// rho <- (rho + rho^+) / (2 tr rho) on the double-float state (FP64 arithmetic; it runs
-// once every `renorm_every` steps), then the FP16 planes again.
+// rho <- (rho + rho^+) / (2 tr rho) (divide != 0) or (rho + rho^+) / 2 on the double-float
+// state (FP64 arithmetic; it runs once every `renorm_every` steps), then the FP16 planes
+// again.
 __global__ void symmetrise_df_kernel(int64_t D, int64_t Dp, float4 *st, const double *tr, const uint32_t *err,
-                                     float s_rho, __half *pl) {
+                                     float s_rho, __half *pl, int divide) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= D || j >= D || j < i) return;
     if (*err & kErrNonFinite) return;
-    const double inv = 1.0 / *tr;
+    const double inv = divide ? 1.0 / *tr : 1.0;
     const float4 a = st[i * D + j], b = st[j * D + i];
     double re = 0.5 * (((double)a.x + (double)a.y) + ((double)b.x + (double)b.y)) * inv;
     double im = 0.5 * (((double)a.z + (double)a.w) - ((double)b.z + (double)b.w)) * inv;
@@ -802,23 +812,9 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         static_assert(kTcMaxAutoSplits <= kTcMaxCluster, "plans must fit the cluster epilogues");
         if (!plan_products(S, S.g1, S.g2, 0, 0, 0)) return QED_ECUDA;
 
-        // per-row phases P_k as double-floats
-        std::vector<double2> ph((size_t)D);
-        QED_CUDA_TRY(cudaMemcpy(ph.data(), m->phase, (size_t)D * sizeof(double2), cudaMemcpyDeviceToHost));
-        std::vector<float4> pdf((size_t)D);
-        for (int64_t k = 0; k < D; ++k) {
-            const float rh = (float)ph[(size_t)k].x, ih = (float)ph[(size_t)k].y;
-            pdf[(size_t)k] = make_float4(rh, (float)(ph[(size_t)k].x - rh), ih, (float)(ph[(size_t)k].y - ih));
-        }
-        QED_CUDA_TRY(cudaMemcpy(S.phase_df, pdf.data(), (size_t)D * sizeof(float4), cudaMemcpyHostToDevice));
-        // dt/2 d_k and sqrt(dt) * coefficient as double-floats
-        auto split_f = [](double x) { const float h = (float)x; return make_float2(h, (float)(x - (double)h)); };
-        std::vector<double> anti((size_t)D);
-        QED_CUDA_TRY(cudaMemcpy(anti.data(), m->anti, (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
-        std::vector<float2> damp((size_t)D);
-        for (int64_t k = 0; k < D; ++k) damp[(size_t)k] = split_f(0.5 * m->dt * anti[(size_t)k]);
         SPLIT_TRY(alloc(&S.damp_df, (size_t)D));
-        QED_CUDA_TRY(cudaMemcpy(S.damp_df, damp.data(), (size_t)D * sizeof(float2), cudaMemcpyHostToDevice));
+        // sqrt(dt) * coefficient of the incoming jump entries as double-floats
+        auto split_f = [](double x) { const float h = (float)x; return make_float2(h, (float)(x - (double)h)); };
         std::vector<double> coef((size_t)m->n_in);
         if (m->n_in > 0)
             QED_CUDA_TRY(cudaMemcpy(coef.data(), m->in_coef, (size_t)m->n_in * sizeof(double), cudaMemcpyDeviceToHost));
@@ -851,8 +847,27 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
         }
     }
     SplitState &S = *m->sp;
+    const bool eff = m->scheme == QED_SCHEME_EFFECTIVE;
+    {
+        // per-row phases P_k and dt/2 d_k (zero for the effective step, whose propagator holds
+        // the anticommutator) as double-floats
+        auto split_f = [](double x) { const float h = (float)x; return make_float2(h, (float)(x - (double)h)); };
+        std::vector<double2> ph((size_t)D);
+        QED_CUDA_TRY(cudaMemcpy(ph.data(), m->phase, (size_t)D * sizeof(double2), cudaMemcpyDeviceToHost));
+        std::vector<float4> pdf((size_t)D);
+        for (int64_t k = 0; k < D; ++k) {
+            const float rh = (float)ph[(size_t)k].x, ih = (float)ph[(size_t)k].y;
+            pdf[(size_t)k] = make_float4(rh, (float)(ph[(size_t)k].x - rh), ih, (float)(ph[(size_t)k].y - ih));
+        }
+        QED_CUDA_TRY(cudaMemcpy(S.phase_df, pdf.data(), (size_t)D * sizeof(float4), cudaMemcpyHostToDevice));
+        std::vector<double> anti((size_t)D);
+        QED_CUDA_TRY(cudaMemcpy(anti.data(), m->anti, (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
+        std::vector<float2> damp((size_t)D);
+        for (int64_t k = 0; k < D; ++k) damp[(size_t)k] = split_f(eff ? 0.0 : 0.5 * m->dt * anti[(size_t)k]);
+        QED_CUDA_TRY(cudaMemcpy(S.damp_df, damp.data(), (size_t)D * sizeof(float2), cudaMemcpyHostToDevice));
+    }
     // Delta into work1, its scales from a host copy, then the constant planes
-    make_delta_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, m->U, m->phase, m->work1);
+    make_delta_kernel<<<blocks_for(D * D, 256), 256, 0, s>>>(D, m->U, m->phase, m->work1, eff ? 0 : 1);
     count_launches(1);
     std::vector<double2> h((size_t)(D * D));
     QED_CUDA_TRY(cudaMemcpyAsync(h.data(), m->work1, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
@@ -889,7 +904,7 @@ qed_status split_begin(qed_model *m, const double2 *rho, cudaStream_t s) {
 
 void split_check_density(qed_model *m, const double2 *rho, cudaStream_t s) {
     dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
-    check_density_kernel<<<grid, dim3(32, 8), 0, s>>>(m->D, rho, m->err);
+    check_density_kernel<<<grid, dim3(32, 8), 0, s>>>(m->D, rho, m->err, m->scheme != QED_SCHEME_EFFECTIVE);
     count_launches(1);
 }
 
@@ -1024,8 +1039,9 @@ void split_renorm(qed_model *m, cudaStream_t s) {
     trace_df_kernel<<<1, 1024, 0, s>>>(m->D, S.rho_df[0], m->scalars, m->err);
     dim3 block(32, 8);
     dim3 grid(blocks_for(m->D, 32), blocks_for(m->D, 8));
+    // the effective step's own trace drift is part of its result: symmetrise only
     symmetrise_df_kernel<<<grid, block, 0, s>>>(m->D, S.Dp, S.rho_df[0], m->scalars, m->err,
-                                                (float)S.scale_rho, S.rho_pl);
+                                                (float)S.scale_rho, S.rho_pl, m->scheme != QED_SCHEME_EFFECTIVE);
     count_launches(2);
 }
 
