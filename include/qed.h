@@ -182,8 +182,8 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every);
  * path's periodic pass symmetrises rho without dividing by its trace (the scheme's own
  * trace drift is part of its result).  EINVAL for an unknown scheme; ENOMEM if a buffer
  * cannot be allocated; ENUMERIC for a singular Pade denominator.  Synchronises the device.
- * qed_adjoint differentiates the Strang step on the FP64 path (EUNSUPPORTED in split
- * precision) and does not differentiate the effective step (EUNSUPPORTED). */
+ * qed_adjoint differentiates the Lie and Strang steps on both paths, not the effective
+ * step (EUNSUPPORTED). */
 qed_status qed_set_scheme(qed_model *m, int32_t scheme);
 
 /* Tile autotuner (the paper has no counterpart: it concerns only how this library maps the
@@ -240,11 +240,12 @@ qed_status qed_evolve(qed_model *m, void *rho, int64_t n_steps, int64_t step_off
  * order of the spec (each may be NULL only if its count is 0).  FP64 models use FP64
  * kernels throughout; split-precision models run the forward steps, the co-state steps
  * (as a backward model with U^+ and the outgoing jump lists) and the products
- * rho_n lambda_n in split precision, accumulating M in FP64.  Under QED_SCHEME_STRANG
- * (FP64 models only; EUNSUPPORTED in split precision) the adjoint of the symmetric step:
- * kappa_n = E^+(lambda_{n+1}), mu_n = U^+ kappa_n U, lambda_n = E^+(mu_n) with E the
- * midpoint half step, M = sum_n E(rho_n) U^+ kappa_n, and the rate gradients of both half
- * steps.  In split precision rho0 must be Hermitian with unit trace (EINVAL otherwise, as
+ * rho_n lambda_n in split precision, accumulating M in FP64.  Under QED_SCHEME_STRANG the
+ * adjoint of the symmetric step, on both paths: kappa_n = E^+(lambda_{n+1}),
+ * mu_n = U^+ kappa_n U, lambda_n = E^+(mu_n) with E the midpoint half step,
+ * M = sum_n E(rho_n) U^+ kappa_n, and the rate gradients of both half steps (in split
+ * precision the backward model runs the same stages; the forward pass keeps rho_n, E(rho_n)
+ * and V_n of a segment).  QED_SCHEME_EFFECTIVE is not differentiated (EUNSUPPORTED).  In split precision rho0 must be Hermitian with unit trace (EINVAL otherwise, as
  * in qed_evolve).  Allocates its work space per call; synchronises `stream`.
  */
 qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_steps, int32_t checkpoint_every,

@@ -609,6 +609,153 @@ qed_status adjoint_split(qed_model *m, const void *rho0, int64_t N, int64_t k, c
     return QED_OK;
 }
 
+// The adjoint of the Strang step in split precision.  Forward: X_n = E(rho_n), V_n =
+// U X_n U^+, rho_{n+1} = E(V_n), E the explicit-midpoint half step (tau = dt/2) of the
+// Lindblad term, run as the model's own stages so that rho_n, X_n and V_n of a segment are
+// kept.  Backward: the twin model (U^+, conjugate phases, the outgoing jump lists, i.e. the
+// adjoint Lindblad term) runs the same stages on the co-state: kappa_n = E^+(lambda_{n+1})
+// (its first stage T = lambda + tau/2 L^+ lambda in the stage buffer), mu_n = U^+ kappa_n U
+// (its V buffer), lambda_n = E^+(mu_n).  M = (sum_n X_n mu_n) U^+ with one FP16 hi/lo
+// tensor-core product per step accumulated in FP64; every rate gradient gets
+// tau tr(T D_j Y) + tau^2/2 tr(Lam D_j(L Y)) from each half step (Lam, Y) = (lambda_{n+1},
+// V_n) and (mu_n, rho_n), L Y applied by the forward model's Lindblad kernel.
+qed_status adjoint_strang_split(qed_model *m, const void *rho0, int64_t N, int64_t k, const double *obs_diag,
+                                double *loss, double *grad_g, double *grad_zeta, double *grad_gamma, cudaStream_t s) {
+    {
+        const qed_status st = make_twin(m, s);
+        if (st != QED_OK) {  // nothing half-built is kept for the next call
+            cudaStreamSynchronize(s);
+            adjoint_release(m);
+            return st;
+        }
+    }
+    AdjointState &a = *m->adj;
+    qed_model *t = a.twin;
+    k = std::min<int64_t>(k, std::max<int64_t>(N, 1));
+    const int64_t D = m->D, Dp = a.Dp;
+    const size_t DD = (size_t)(D * D);
+    const int64_t n_ck = N > 0 ? (N - 1) / k + 1 : 0;
+    const double dt = m->dt, tau = 0.5 * dt;
+    // the co-state runs for o / 2^e (see adjoint_split)
+    std::vector<double> ho((size_t)D);
+    QED_CUDA_TRY(cudaMemcpyAsync(ho.data(), obs_diag, (size_t)D * 8, cudaMemcpyDeviceToHost, s));
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    double omax = 0.0;
+    for (double x : ho) omax = std::max(omax, std::abs(x));
+    const int e = omax > 0.0 ? (int)std::ceil(std::log2(omax)) : 0;
+    const double o_scale = std::ldexp(1.0, e);
+    for (double &x : ho) x = std::ldexp(x, -e);
+    const double s_a = std::ldexp(1.0, 14), s_b = std::ldexp(1.0, 14);
+    Buffers B;
+    float4 *ck = nullptr, *seg_rho = nullptr, *seg_x = nullptr, *seg_v = nullptr, *Ly = nullptr;
+    double2 *Nacc = nullptr, *Macc = nullptr;
+    double *r = nullptr, *o_s = nullptr;
+    ADJ_TRY(B.get(&o_s, (size_t)D));
+    QED_CUDA_TRY(cudaMemcpyAsync(o_s, ho.data(), (size_t)D * 8, cudaMemcpyHostToDevice, s));
+    ADJ_TRY(B.get(&ck, DD * (size_t)std::max<int64_t>(n_ck, 1)));
+    ADJ_TRY(B.get(&seg_rho, DD * (size_t)k));
+    ADJ_TRY(B.get(&seg_x, DD * (size_t)k));
+    ADJ_TRY(B.get(&seg_v, DD * (size_t)k));
+    ADJ_TRY(B.get(&Ly, DD));
+    ADJ_TRY(B.get(&Nacc, DD));
+    ADJ_TRY(B.get(&Macc, DD));
+    ADJ_TRY(B.get(&r, (size_t)D));
+    auto copy = [&](float4 *dst, const float4 *src) {
+        return cudaMemcpyAsync(dst, src, DD * 16, cudaMemcpyDeviceToDevice, s);
+    };
+    // one forward step of the state (in place), keeping X_n and V_n when asked
+    auto fwd_step = [&](float4 *x_out, float4 *v_out) -> cudaError_t {
+        split_lindblad_stage(m, 0, 0, 2, 0.25f, 0, s);  // Y = rho + dt/4 L(rho)
+        split_lindblad_stage(m, 2, 0, 0, 0.5f, 1, s);   // X_n = rho + dt/2 L(Y), and its planes
+        cudaError_t ce = x_out ? copy(x_out, split_state(m)) : cudaSuccess;
+        split_products(m, s);                           // V_n = U X_n U^+
+        if (ce == cudaSuccess && v_out) ce = copy(v_out, split_vbuf(m));
+        split_lindblad_stage(m, 1, 1, 2, 0.25f, 0, s);
+        split_lindblad_stage(m, 2, 1, 0, 0.5f, 0, s);   // rho_{n+1} = E(V_n)
+        return ce;
+    };
+    auto rate = [&](const float4 *Lam, const float4 *Y, double scale) {
+        rowdot_df_kernel<<<blocks_for(D, 8), 256, 0, s>>>(D, Lam, Y, r);
+        gamma_grad_df_kernel<<<a.n_jumps, 256, 0, s>>>(D, a.je_ptr, a.je_src, a.je_dst, a.je_coef, Lam, Y, r, scale,
+                                                       grad_gamma);
+        count_launches(2);
+    };
+    const int64_t last0 = (n_ck - 1) * k;  // the last segment is stored by the forward pass
+    split_check_density(m, (const double2 *)rho0, s);
+    ADJ_TRY(split_begin(m, (const double2 *)rho0, s));
+    for (int64_t n = 0; n < N; ++n) {
+        if (n % k == 0 && n < last0) QED_CUDA_TRY(copy(ck + (size_t)(n / k) * DD, split_state(m)));
+        const bool keep = n >= last0;
+        const size_t o = keep ? (size_t)(n - last0) * DD : 0;
+        if (keep) QED_CUDA_TRY(copy(seg_rho + o, split_state(m)));
+        QED_CUDA_TRY(fwd_step(keep ? seg_x + o : nullptr, keep ? seg_v + o : nullptr));
+    }
+    loss_df_kernel<<<1, 256, 0, s>>>(D, split_state(m), obs_diag, loss);
+    set_diag_df_kernel<<<blocks_for((int64_t)DD, 256), 256, 0, s>>>(D, o_s, split_state(t));  // lambda_N
+    count_launches(2);
+    QED_CUDA_TRY(cudaMemsetAsync(Nacc, 0, DD * 16, s));
+    if (a.n_jumps > 0) QED_CUDA_TRY(cudaMemsetAsync(grad_gamma, 0, (size_t)a.n_jumps * 8, s));
+    const dim3 rows(blocks_for(D, 256), (unsigned)D);
+    const double r1 = o_scale * tau, r2 = o_scale * 0.5 * tau * tau / dt;  // Ly holds dt L(Y)
+    for (int64_t c = n_ck - 1; c >= 0; --c) {
+        const int64_t s0 = c * k, s1 = std::min(N, s0 + k);
+        if (c < n_ck - 1) {  // recompute the segment, keeping rho_n, X_n and V_n
+            QED_CUDA_TRY(copy(split_state(m), ck + (size_t)c * DD));
+            for (int64_t n = s0; n < s1; ++n) {
+                const size_t o = (size_t)(n - s0) * DD;
+                QED_CUDA_TRY(copy(seg_rho + o, split_state(m)));
+                QED_CUDA_TRY(fwd_step(seg_x + o, seg_v + o));
+            }
+        }
+        for (int64_t n = s1 - 1; n >= s0; --n) {
+            const size_t o = (size_t)(n - s0) * DD;
+            const float4 *rn = seg_rho + o, *xn = seg_x + o, *vn = seg_v + o;
+            // kappa_n = E^+(lambda_{n+1}) with the rate terms of the trailing half step
+            if (a.n_jumps > 0) {
+                split_apply_lindblad(m, vn, Ly, s);
+                rate(split_state(t), Ly, r2);
+            }
+            split_lindblad_stage(t, 0, 0, 2, 0.25f, 0, s);
+            if (a.n_jumps > 0) rate(split_ybuf(t), vn, r1);
+            split_lindblad_stage(t, 2, 0, 0, 0.5f, 1, s);
+            // mu_n = U^+ kappa_n U;  Nacc += X_n mu_n on the tensor cores
+            split_products(t, s);
+            a_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, xn, (float)s_a, a.a_pl);
+            b_planes_kernel<<<rows, 256, 0, s>>>(D, Dp, split_vbuf(t), (float)s_b, a.b_pl);
+            count_launches(2);
+            QED_CUDA_TRY(tc_gemm_launch(a.g, a.c_slices, m->err, s));
+            acc_kernel<<<rows, 256, 0, s>>>(D, Dp, a.g.splits, a.c_slices, o_scale / (s_a * s_b), Nacc);
+            count_launches(1);
+            // lambda_n = E^+(mu_n) with the rate terms of the leading half step
+            if (a.n_jumps > 0) {
+                split_apply_lindblad(m, rn, Ly, s);
+                rate(split_vbuf(t), Ly, r2);
+            }
+            split_lindblad_stage(t, 1, 1, 2, 0.25f, 0, s);
+            if (a.n_jumps > 0) rate(split_ybuf(t), rn, r1);
+            split_lindblad_stage(t, 2, 1, 0, 0.5f, 0, s);
+        }
+    }
+    // M = Nacc U^+, then the Frechet contraction
+    zgemm(s, D, D, D, 1.0, Nacc, D, m->U, D, true, 0.0, Macc, D);
+    ADJ_TRY(frechet_gradients(m, B, Macc, grad_g, grad_zeta, s));
+    uint32_t flags[2] = {0, 0};
+    QED_CUDA_TRY(cudaMemcpy(&flags[0], m->err, 4, cudaMemcpyDeviceToHost));
+    QED_CUDA_TRY(cudaMemcpy(&flags[1], t->err, 4, cudaMemcpyDeviceToHost));
+    if ((flags[0] | flags[1]) & kErrTimeout) {
+        QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+        QED_CUDA_TRY(cudaMemset(t->err, 0, 4));
+        set_error("qed_adjoint: a bounded device wait ran out");
+        return QED_ETIMEOUT;
+    }
+    if (flags[0] & kErrNotDensity) {
+        QED_CUDA_TRY(cudaMemset(m->err, 0, 4));
+        set_error("qed_adjoint: split precision needs a Hermitian rho0 of unit trace");
+        return QED_EINVAL;
+    }
+    return QED_OK;
+}
+
 // The adjoint of the Strang step on the FP64 path.  Forward: X_n = E(rho_n),
 // V_n = U X_n U^+, rho_{n+1} = E(V_n), E the explicit-midpoint half step (tau = dt/2) of the
 // Lindblad term.  Backward: kappa_n = E^+(lambda_{n+1}), mu_n = U^+ kappa_n U,
@@ -744,10 +891,6 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: the effective-Hamiltonian step is not differentiated");
         return QED_EUNSUPPORTED;
     }
-    if (m->scheme != QED_SCHEME_LIE && m->prec != QED_FP64) {
-        set_error("qed_adjoint: the Strang step is differentiated on the FP64 path only");
-        return QED_EUNSUPPORTED;
-    }
     {
         // a failed set-up (e.g. out of device memory) leaves no half-built tables behind
         const qed_status st = setup(m);
@@ -762,6 +905,9 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         return QED_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (m->prec != QED_FP64 && m->scheme == QED_SCHEME_STRANG)
+        return adjoint_strang_split(m, rho0, n_steps, checkpoint_every, obs_diag, loss, grad_g, grad_zeta, grad_gamma,
+                                    s);
     if (m->prec != QED_FP64)
         return adjoint_split(m, rho0, n_steps, checkpoint_every, obs_diag, loss, grad_g, grad_zeta, grad_gamma, s);
     if (m->scheme == QED_SCHEME_STRANG)

@@ -349,7 +349,8 @@ __device__ __forceinline__ void damping_term(float2 dm, float2 dn, const cdf &v,
 template <bool LIE>
 __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ tiles,
                                                 const InstDesc *__restrict__ descs, int xsel, int bsel, int osel,
-                                                float f, bool planes) {
+                                                float f, bool planes, const float4 *X_only = nullptr,
+                                                float4 *O_only = nullptr) {
     // set-up tables (damping, padded jump rows) are read while the previous kernel finishes
     const TileItem it = tiles[blockIdx.x];
     const InstDesc a = descs[it.inst];
@@ -359,9 +360,10 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     const bool n_in = n < D;
     const int64_t nc = n_in ? n : 0;
     const float2 dn = a.damp[nc];
-    const float4 *X = LIE ? a.V : state_buf(a, xsel);
-    const float4 *B = LIE ? a.V : state_buf(a, bsel);
-    float4 *O = LIE ? a.rho : state_buf(a, osel);
+    // X_only: out = f dt L(X_only) into O_only (B = 0), for buffers outside the model
+    const float4 *X = X_only ? X_only : (LIE ? a.V : state_buf(a, xsel));
+    const float4 *B = X_only ? nullptr : (LIE ? a.V : state_buf(a, bsel));
+    float4 *O = X_only ? O_only : (LIE ? a.rho : state_buf(a, osel));
     if (a.in_tab) {
         // padded incoming tables: the row entries are the same for the whole warp (one row per
         // warp and r), the column's for all kRows rows of the thread
@@ -419,7 +421,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
                 gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
                 gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
             }
-            const cdf b = LIE ? vv : load_cdf(B[m * D + n]);
+            const cdf b = LIE ? vv : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
             lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
         }
         return;
@@ -461,7 +463,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
             }
         }
         if (!inside) continue;
-        const cdf b = LIE ? v : load_cdf(B[m * D + n]);
+        const cdf b = LIE ? v : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
         lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
     }
 }
@@ -477,6 +479,13 @@ __global__ void __launch_bounds__(256, 2) lindblad_df_kernel(const TileItem *__r
                                                           const InstDesc *__restrict__ descs, int xsel, int bsel,
                                                           int osel, float f, int planes) {
     lindblad_update<false>(tiles, descs, xsel, bsel, osel, f, planes != 0);
+}
+
+// out = dt L(X) for a double-float buffer X of a single model (the adjoint's rate terms).
+__global__ void __launch_bounds__(256, 2) lindblad_apply_df_kernel(const TileItem *__restrict__ tiles,
+                                                                const InstDesc *__restrict__ descs,
+                                                                const float4 *X, float4 *out) {
+    lindblad_update<false>(tiles, descs, 0, 0, 0, 1.f, false, X, out);
 }
 
 __global__ void __launch_bounds__(256) observables_df_kernel(int64_t D, const float4 *st, const double *w,
@@ -992,6 +1001,23 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
              std::to_string(1e3 * best / steps) + " us per step";
     return QED_OK;
 }
+
+void split_lindblad_stage(qed_model *m, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s) {
+    launch_lindblad(m->sp->self, xsel, bsel, osel, f, planes, s);
+}
+
+void split_apply_lindblad(qed_model *m, const float4 *X, float4 *out, cudaStream_t s) {
+    const Batch &b = m->sp->self;
+    launch_pdl(lindblad_apply_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc, X, out);
+    count_launches(1);
+}
+
+void split_products(qed_model *m, cudaStream_t s) {
+    launch_gemm1(m->sp->self, m->err, s);
+    launch_gemm2(m->sp->self, m->err, s);
+}
+
+float4 *split_ybuf(qed_model *m) { return m->sp->y_df; }
 
 qed_status split_rebuild(qed_model *m, cudaStream_t s) {
     QED_CUDA_TRY(cudaStreamSynchronize(s));

@@ -33,6 +33,14 @@ void split_populations(qed_model *m, double *out, cudaStream_t s);      // out[k
 float4 *split_state(qed_model *m);
 float4 *split_vbuf(qed_model *m);
 void split_dissipate_only(qed_model *m, cudaStream_t s);
+// The pieces of a step, for the adjoint of the Strang step: one Lindblad stage
+// out = B + f dt L(X) on the model's buffers (0 state, 1 V buffer, 2 stage buffer; planes:
+// also write the state's FP16 planes), out = dt L(X) for any double-float D x D buffer X,
+// the two products V = U X U^+ of the state X (planes already written), the stage buffer.
+void split_lindblad_stage(qed_model *m, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s);
+void split_apply_lindblad(qed_model *m, const float4 *X, float4 *out, cudaStream_t s);
+void split_products(qed_model *m, cudaStream_t s);
+float4 *split_ybuf(qed_model *m);
 void split_refresh_planes(qed_model *m, cudaStream_t s);
 
 // Many split-precision models stepped together: one grouped launch per phase.
