@@ -44,6 +44,8 @@ struct InstDesc {
     const int32_t *in_ptr, *in_jump, *in_src;
     const float2 *coef;
     const int4 *in_tab;     // [D][kInMax] {jump, src, coef hi, coef lo} or null (use the lists)
+    const int4 *jtab;       // [D][kInMax] per jump j < nj: {src or -1, coef hi, coef lo, 0}, or null
+    int nj;
     __half *rho_pl;
 };
 
@@ -104,6 +106,8 @@ struct SplitState {
     float2 *damp_df = nullptr;               // D: dt/2 * d_k as {hi, lo}
     float2 *coef_df = nullptr;               // incoming jump entries: sqrt(dt) * coefficient
     int4 *in_tab = nullptr;                  // padded incoming table (rows with <= kInMax entries)
+    int4 *jtab = nullptr;                    // per-jump incoming table (at most kInMax jumps)
+    int nj = 0;
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
 };
 
@@ -364,6 +368,58 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     const float4 *X = X_only ? X_only : (LIE ? a.V : state_buf(a, xsel));
     const float4 *B = X_only ? nullptr : (LIE ? a.V : state_buf(a, bsel));
     float4 *O = X_only ? O_only : (LIE ? a.rho : state_buf(a, osel));
+    if (a.jtab) {
+        // incoming entries by jump: element (m, n) gets c_j(m) c_j(n) X[src_j(m), src_j(n)] for
+        // every jump j with an entry in both rows (row entries warp-uniform, column entries
+        // read once for the thread's kRows rows)
+        const int nj = a.nj;
+        int4 tn[kInMax], tm[kRows][kInMax];
+        float2 dm[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r, mc = m < D ? m : 0;
+            dm[r] = a.damp[mc];
+#pragma unroll
+            for (int j = 0; j < kInMax; ++j)
+                tm[r][j] = j < nj ? a.jtab[mc * kInMax + j] : make_int4(-1, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < kInMax; ++j) tn[j] = j < nj ? a.jtab[nc * kInMax + j] : make_int4(-1, 0, 0, 0);
+        pdl_wait();
+        pdl_trigger();
+        float4 v[kRows], u[kRows][kInMax];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r;
+            const bool inside = m < D && n_in;
+            v[r] = X[(inside ? m : 0) * D + nc];
+#pragma unroll
+            for (int j = 0; j < kInMax; ++j) {
+                const bool hit = inside && tm[r][j].x >= 0 && tn[j].x >= 0;
+                u[r][j] = hit ? X[(int64_t)tm[r][j].x * D + tn[j].x] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const int64_t m = m0 + 8 * r;
+            if (!(m < D && n_in)) continue;
+            const cdf vv = load_cdf(v[r]);
+            float gr, gi;
+            damping_term(dm[r], dn, vv, gr, gi);
+#pragma unroll
+            for (int j = 0; j < kInMax; ++j) {
+                if (!(tm[r][j].x >= 0 && tn[j].x >= 0)) continue;
+                const df c = df_mul({__int_as_float(tm[r][j].y), __int_as_float(tm[r][j].z)},
+                                    {__int_as_float(tn[j].y), __int_as_float(tn[j].z)});
+                const float ur = u[r][j].x + u[r][j].y, ui = u[r][j].z + u[r][j].w;
+                gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
+                gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
+            }
+            const cdf b = LIE ? vv : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
+            lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
+        }
+        return;
+    }
     if (a.in_tab) {
         // padded incoming tables: the row entries are the same for the whole warp (one row per
         // warp and r), the column's for all kRows rows of the thread
@@ -649,6 +705,8 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.in_src = m->in_src;
         d.coef = S.coef_df;
         d.in_tab = S.in_tab;
+        d.jtab = S.jtab;
+        d.nj = S.nj;
         d.rho_pl = S.rho_pl;
         TcGemm bg1 = S.g1, bg2 = S.g2;
         if (!single && !plan_products(S, bg1, bg2, 1, kTcBNMax, 1)) return QED_ECUDA;
@@ -853,6 +911,32 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
                 }
             SPLIT_TRY(alloc(&S.in_tab, tab.size()));
             QED_CUDA_TRY(cudaMemcpy(S.in_tab, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        }
+        // with at most kInMax jumps, and (monomial operators) at most one incoming entry per
+        // state and jump, the entries indexed by jump: the Lindblad kernels then read the
+        // pairs (m, n) of each jump directly instead of matching the two rows' lists
+        const int nj = (int)m->host.gamma.size();
+        if (nj >= 1 && nj <= kInMax) {
+            std::vector<int4> jt((size_t)D * kInMax, make_int4(-1, 0, 0, 0));
+            bool unique = true;
+            for (int64_t k = 0; k < D && unique; ++k)
+                for (int32_t e = ptr[(size_t)k]; e < ptr[(size_t)k + 1]; ++e) {
+                    int4 &slot = jt[(size_t)(k * kInMax + jmp[(size_t)e])];
+                    if (slot.x >= 0) {
+                        unique = false;
+                        break;
+                    }
+                    const float2 c = cdf_[(size_t)e];
+                    int f_hi = 0, f_lo = 0;
+                    std::memcpy(&f_hi, &c.x, 4);
+                    std::memcpy(&f_lo, &c.y, 4);
+                    slot = make_int4(src[(size_t)e], f_hi, f_lo, 0);
+                }
+            if (unique) {
+                SPLIT_TRY(alloc(&S.jtab, jt.size()));
+                QED_CUDA_TRY(cudaMemcpy(S.jtab, jt.data(), jt.size() * sizeof(int4), cudaMemcpyHostToDevice));
+                S.nj = nj;
+            }
         }
     }
     SplitState &S = *m->sp;
@@ -1129,7 +1213,7 @@ void split_release(qed_model *m) {
     SplitState &S = *m->sp;
     S.self.release();
     void *ptrs[] = {S.a1,       S.b2,       S.rho_pl,   S.w_pl,    S.w32,    S.rho_df[0], S.rho_df[1],
-                    S.phase_df, S.damp_df, S.coef_df, S.in_tab, S.y_df};
+                    S.phase_df, S.damp_df, S.coef_df, S.in_tab, S.y_df, S.jtab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete m->sp;
