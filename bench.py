@@ -370,9 +370,10 @@ def dissipator_roofline(kern, D):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the named kernel, from one ncu
-# capture of the current kernel on the dim-512 step (the capture is summarised under
-# profiles/ and named in the design notes); None when no capture of the current kernel exists
-GEMM1_DRAM_BYTES = {}
+# capture of the current kernel on the dim-512 step with L2 flushed before the launch
+# (profiles/split_step_hb_shaped_d512_full.md): the operand planes read once, nothing
+# re-read.  None when no capture of the current kernel exists.
+GEMM1_DRAM_BYTES = {("gemm1_tc", 512): 8420864 + 0}
 
 
 def make_roofline(kern, D, precision):
