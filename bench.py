@@ -370,9 +370,9 @@ def dissipator_roofline(kern, D):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the named kernel, from one ncu
-# capture of the current kernel on the dim-512 step with L2 flushed before the launch
-# (profiles/split_step_hb_shaped_d512_full.md): the operand planes read once, nothing
-# re-read.  None when no capture of the current kernel exists.
+# capture of the current kernel on the dim-512 step with L2 flushed before the launch (the
+# operand planes read once, nothing re-read).  None when no capture of the current kernel
+# exists.
 GEMM1_DRAM_BYTES = {("gemm1_tc", 512): 8420864 + 0}
 
 
@@ -441,10 +441,12 @@ def _basis_rho0(gm, dev):
 
 
 def measure_workload(wl, precision, scheme, dev, flush, warmup=3, steps=1, instances=512, qme_steps=None,
-                     selection_eps=1e-20, selection_round=100):
+                     selection_eps=1e-20, selection_round=100, autotune=False):
     """Times one workload other than the headline through the public API and compares its
     result with the stored oracle values where they exist (tests/golden: written by a script
-    that calls only the oracle).  Returns a dict: value, unit, rates, parity, config."""
+    that calls only the oracle).  With `autotune` the split-precision tile plan is timed and
+    chosen first (qed_autotune / qed_autotune_batched, outside the timed region).  Returns a
+    dict: value, unit, rates, parity, config."""
     import torch
 
     import paper_2403_07042_gb300 as qed
@@ -460,6 +462,8 @@ def measure_workload(wl, precision, scheme, dev, flush, warmup=3, steps=1, insta
         models = [qed.Model(m, precision=precision, scheme=scheme) for m in specs]
         extra["model_build_s"] = time.perf_counter() - t_build
         dims = [gm.dim for gm in models]
+        if autotune and precision != "fp64":
+            extra["autotuned"] = qed.autotune_batched(models, steps=3)
         rho0 = [_basis_rho0(gm, dev) for gm in models]
         rhos = [x.clone() for x in rho0]
         recs = [torch.zeros((n // r + 1, d), dtype=torch.float64, device=dev) for d in dims]
@@ -496,6 +500,8 @@ def measure_workload(wl, precision, scheme, dev, flush, warmup=3, steps=1, insta
         gm = qed.Model(m, precision=precision, scheme=scheme)
         # basis, operators and U = exp(-i H dt) (the "Taylor approximation" stage of Table 3)
         extra["model_build_s"] = time.perf_counter() - t_build
+        if autotune and precision != "fp64" and wl != "selection_hb_shaped_d512":
+            extra["autotuned"] = gm.autotune(10)
         D = gm.dim
         rho0 = _basis_rho0(gm, dev)
         rho = rho0.clone()
@@ -600,7 +606,7 @@ def run_secondary(dev, flush):
     out = {}
     for wl, prec in SECONDARY:
         try:
-            out[f"{wl}_{prec}"] = measure_workload(wl, prec, "lie", dev, flush)
+            out[f"{wl}_{prec}"] = measure_workload(wl, prec, "lie", dev, flush, autotune=True)
         except Exception as e:  # reported, not hidden: the line still carries the headline
             out[f"{wl}_{prec}"] = {"error": f"{type(e).__name__}: {e}"}
         gc.collect()
@@ -623,7 +629,8 @@ def run_other(args):
     sampler.start()
     r = measure_workload(args.workload, args.precision, args.scheme, dev, flush, warmup=args.warmup,
                          steps=args.steps, instances=args.instances, qme_steps=args.qme_steps,
-                         selection_eps=args.selection_eps, selection_round=args.selection_round)
+                         selection_eps=args.selection_eps, selection_round=args.selection_round,
+                         autotune=args.autotune)
     clocks = sampler.stop()
     line = {
         "metric": METRIC, "value": r["value"], "unit": r["unit"], "n_gpus": 1, "steps": args.steps,

@@ -197,6 +197,17 @@ qed_status qed_set_scheme(qed_model *m, int32_t scheme);
  * have nothing to tune (OK).  EINVAL for steps <= 0. */
 qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choice_cap, qed_stream stream);
 
+/* The batched counterpart (no counterpart in the paper either): the grouped launches of
+ * qed_evolve_batched share one tile plan, so this times `steps` whole batched steps of the
+ * n split-precision models `ms` for each GEMM1 tile width (256 and 128 columns; both
+ * products unsplit, GEMM2 128-wide) and stores the fastest in every model; a later
+ * qed_evolve_batched uses it when all its models carry the same width (else 256).  The
+ * models' internal states are zeroed and used as scratch (qed_evolve_batched imports rho
+ * again); synchronises the stream.  Writes the choice and the timings into `choice` (size
+ * choice_cap; may be NULL).  EINVAL for n <= 0, steps <= 0, a NULL, repeated or FP64 model. */
+qed_status qed_autotune_batched(int32_t n, qed_model *const *ms, int32_t steps, char *choice, int32_t choice_cap,
+                                qed_stream stream);
+
 /* ---------------------------------------------------------------- hot path */
 
 /*

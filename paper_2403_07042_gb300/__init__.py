@@ -80,6 +80,7 @@ def lib():
         "qed_set_renorm_every": [vp, i32],
         "qed_set_scheme": [vp, i32],
         "qed_autotune": [vp, i32, ctypes.c_char_p, i32, vp],
+        "qed_autotune_batched": [i32, ctypes.POINTER(vp), i32, ctypes.c_char_p, i32, vp],
         "qed_evolve": [vp, vp, i64, i64, i32, i32, _c_int32_p, vp, vp],
         "qed_observables": [vp, vp, i32, _c_int32_p, vp, vp],
         "qed_sync_status": [vp, vp],
@@ -473,6 +474,16 @@ def evolve_batched(models, rhos, n_steps, record_every=0, records=None, stream=N
     _check(lib().qed_evolve_batched(n, H, R, int(n_steps), int(record_every), rec, _stream_handle(stream)),
            "qed_evolve_batched")
     return records
+
+
+def autotune_batched(models, steps=3, stream=None):
+    """Times the GEMM1 tile widths of the grouped launches on whole batched steps of these
+    models (qed_autotune_batched) and keeps the fastest in them; returns the description."""
+    n = len(models)
+    H = (ctypes.c_void_p * n)(*[m._h.value for m in models])
+    buf = ctypes.create_string_buffer(256)
+    _check(lib().qed_autotune_batched(n, H, int(steps), buf, 256, _stream_handle(stream)), "qed_autotune_batched")
+    return buf.value.decode()
 
 
 def select_states(model, rho0, steps_per_round, n_rounds, eps, stream=None):

@@ -505,6 +505,25 @@ qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choic
     return QED_OK;
 }
 
+qed_status qed_autotune_batched(int32_t n, qed_model *const *ms, int32_t steps, char *choice, int32_t choice_cap,
+                                qed_stream stream) {
+    if (n <= 0 || !ms || steps <= 0) return einval("qed_autotune_batched: need n > 0 models and steps > 0");
+    for (int32_t i = 0; i < n; ++i) {
+        if (!ms[i]) return einval("qed_autotune_batched: NULL model");
+        if (ms[i]->prec == QED_FP64) return einval("qed_autotune_batched: FP64 instances have no grouped launches");
+        for (int32_t j = 0; j < i; ++j)
+            if (ms[j] == ms[i]) return einval("qed_autotune_batched: a model appears twice");
+    }
+    std::string c;
+    QED_TRY(split_autotune_batched(ms, n, (cudaStream_t)stream, steps, c));
+    for (int32_t i = 0; i < n; ++i) QED_TRY(qed_sync_status(ms[i], stream));
+    if (choice && choice_cap > 0) {
+        std::strncpy(choice, c.c_str(), (size_t)choice_cap - 1);
+        choice[choice_cap - 1] = 0;
+    }
+    return QED_OK;
+}
+
 qed_status qed_set_wait_gate(qed_model *m, int32_t closed, int64_t budget_cycles, qed_stream stream) {
     if (!m || budget_cycles < 0) return einval("qed_set_wait_gate: NULL model or negative budget");
     if (m->prec == QED_FP64) {

@@ -496,6 +496,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     volatile int *consumed = abort_flag + 2;  // stage loads the MMA issuer has waited for
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // a 256-wide tile with 128 columns of the product left (the last tile when N is an odd
+    // multiple of 128) computes only those
+    const bool narrow = BN == 256 && p.N - tile_n * BN <= BN / 2;
     const int kb0 = split * p.kb_per_split;
     const int nkb = min(p.kb_per_split, p.kb_total - kb0);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages),
@@ -588,8 +591,10 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
             *issued = i + 1;
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_f16(kTcBM, kTcBN);
+        // MMA issuer; a 256-wide tile with only 128 columns left before N (N is a multiple of
+        // 128) issues 128-wide MMAs: the other half of its B box is the TMA's zero fill
+        const uint32_t idesc =
+            narrow ? idesc_f16(kTcBM, kTcBN / 2) : idesc_f16(kTcBM, kTcBN);
         for (int i = 0; i < nkb; ++i) {
             if (*abort_flag) break;  // the stages already issued are drained at the end
             const int s = i % kTcStages;
@@ -679,8 +684,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
         if (ok) {
             const int c0 = (warp >> 2) * cols;
             const bool corr = p.nseg > 1;
+            const int c_end = narrow ? min(c0 + cols, BN / 2) : c0 + cols;  // columns the MMAs wrote
 #pragma unroll 1
-            for (int c = c0; c < c0 + cols; c += 32) {
+            for (int c = c0; c < c_end; c += 32) {
                 uint32_t mv[32], cv[32];
                 tmem_ld32_async(tm_row + (uint32_t)c, mv);
                 tmem_ld32_async(tm_row + (uint32_t)(BN + c), cv);

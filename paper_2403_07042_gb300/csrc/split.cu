@@ -109,6 +109,7 @@ struct SplitState {
     int4 *jtab = nullptr;                    // per-jump incoming table (at most kInMax jumps)
     int nj = 0;
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
+    int batch_bn1 = kTcBNMax;  // GEMM1 tile width of the grouped launches (qed_autotune_batched)
 };
 
 namespace {
@@ -673,7 +674,7 @@ bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, 
 // product runs unsplit, largest first, since the batch itself fills the GPU.  GEMM1 skips
 // tiles that lie wholly in the zero padding (rows or columns >= D); GEMM2 runs the tiles on
 // or above the diagonal only (its epilogue writes both halves of the Hermitian V).
-qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
+qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int batch_bn1 = kTcBNMax) {
     b.release();
     b.n = n;
     b.scheme = ms[0]->scheme;
@@ -709,7 +710,7 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single) {
         d.nj = S.nj;
         d.rho_pl = S.rho_pl;
         TcGemm bg1 = S.g1, bg2 = S.g2;
-        if (!single && !plan_products(S, bg1, bg2, 1, kTcBNMax, 1)) return QED_ECUDA;
+        if (!single && !plan_products(S, bg1, bg2, 1, batch_bn1, 1)) return QED_ECUDA;
         auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
         if (!pow2(bg1.splits) || bg1.splits > kTcMaxCluster || !pow2(bg2.splits) || bg2.splits > kTcMaxClusterV ||
             bg2.bn != 128) {
@@ -1086,6 +1087,54 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
     return QED_OK;
 }
 
+// The batched counterpart: the grouped launches share one plan, so the candidates are the
+// tile widths of GEMM1 (128, 256; unsplit, GEMM2 128-wide), each timed on `steps` whole
+// batched steps from a zero state.  The winner is kept in every model of the batch.
+qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, int steps, std::string &choice) {
+    for (int i = 0; i < n; ++i) {
+        SplitState &S = *ms[i]->sp;
+        QED_CUDA_TRY(cudaMemsetAsync(S.rho_df[0], 0, (size_t)(ms[i]->D * ms[i]->D) * sizeof(float4), s));
+        QED_CUDA_TRY(cudaMemsetAsync(S.rho_pl, 0, (size_t)S.Dp * 2 * S.Dp * 2 * sizeof(__half), s));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QED_CUDA_TRY(cudaEventCreate(&e0));
+    QED_CUDA_TRY(cudaEventCreate(&e1));
+    Batch b;
+    qed_status st = QED_OK;
+    float best = -1.f;
+    int best_bn = kTcBNMax;
+    std::string times;
+    for (int bn : {256, 128}) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error(std::string("autotune (batched): ") + cudaGetErrorString(cudaGetLastError()));
+            st = QED_ECUDA;
+            break;
+        }
+        if ((st = build_batch(b, ms, n, false, bn)) != QED_OK) break;
+        for (int i = 0; i < 2; ++i) batch_step(b, ms[0]->err, s);
+        float t = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = QED_ECUDA; break; }
+        for (int i = 0; i < steps; ++i) batch_step(b, ms[0]->err, s);
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            set_error(std::string("autotune (batched): ") + cudaGetErrorString(cudaGetLastError()));
+            st = QED_ECUDA;
+            break;
+        }
+        times += (times.empty() ? "" : ", ") + std::to_string(bn) + "-wide " + std::to_string(1e3 * t / steps) +
+                 " us";
+        if (best < 0.f || t < best) best = t, best_bn = bn;
+    }
+    cudaStreamSynchronize(s);
+    b.release();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != QED_OK) return st;
+    for (int i = 0; i < n; ++i) ms[i]->sp->batch_bn1 = best_bn;
+    choice = "gemm1 " + std::to_string(best_bn) + "-wide (batched step: " + times + ")";
+    return QED_OK;
+}
+
 void split_lindblad_stage(qed_model *m, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s) {
     launch_lindblad(m->sp->self, xsel, bsel, osel, f, planes, s);
 }
@@ -1180,7 +1229,11 @@ void split_populations(qed_model *m, double *out, cudaStream_t s) {
 
 qed_status split_batch_create(qed_model *const *ms, int n, Batch **out) {
     Batch *b = new Batch();
-    qed_status st = build_batch(*b, ms, n, false);
+    // the tuned tile width when every model of the batch carries the same one
+    int bn1 = ms[0]->sp->batch_bn1;
+    for (int i = 1; i < n; ++i)
+        if (ms[i]->sp->batch_bn1 != bn1) bn1 = kTcBNMax;
+    qed_status st = build_batch(*b, ms, n, false, bn1);
     if (st != QED_OK) {
         b->release();
         delete b;

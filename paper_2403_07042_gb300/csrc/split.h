@@ -48,6 +48,9 @@ struct Batch;
 qed_status split_batch_create(qed_model *const *ms, int n, Batch **out);
 void split_batch_step(const Batch *b, uint32_t *err, cudaStream_t s);
 void split_batch_destroy(Batch *b);
+// Times the grouped launches' tile widths on whole batched steps; keeps the fastest in the
+// models (used by the next split_batch_create of models that all carry it).
+qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, int steps, std::string &choice);
 void split_release(qed_model *m);
 
 }  // namespace qed

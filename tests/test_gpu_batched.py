@@ -112,6 +112,30 @@ def test_batched_chains_full_size_against_stored_oracle(precision, tol_rho, tol_
           f"max|dpop| = {worst_p:.2e}")
 
 
+def test_batched_chains_full_size_fp64_own_U():
+    """The first six instances of the same workload in FP64 with the GPU's own Pade U (no
+    qed_set_U), against the same stored oracle trajectories (the oracle's eigendecomposition
+    U).  The step maps differ by dU = U_gpu - U_oracle; each step moves the state by at most
+    2 ||dU||_2 (unit-trace rho) and the Lindblad part and later steps do not enlarge that, so
+    after n steps the gap is at most 2 n ||dU||_2 plus the rounding bound 2 n D u above."""
+    g = np.load(os.path.join(GOLDEN, "batched_chains_d53_1008_oracle.npz"))
+    specs = W.batched_chains(int(g["n"]), seed=0)[:6]
+    models, rhos = _setup(specs, "fp64")
+    dUs = []
+    for m, gm in zip(specs, models):
+        U = _oracle_U(m, oracle.enumerate_basis(m))
+        dUs.append(np.linalg.norm(gm.get_U().cpu().numpy() - U, 2))
+        assert dUs[-1] <= 1e-14
+    recs = qed.evolve_batched(models, rhos, 1000, record_every=100)
+    torch.cuda.synchronize()
+    for i, (gm, r, rec) in enumerate(zip(models, rhos, recs)):
+        rows = g[f"rows_{i}"]
+        err = np.abs(r.cpu().numpy()[rows] - g[f"rho_rows_{i}"]).max()
+        perr = np.abs(rec.cpu().numpy() - g[f"records_{i}"]).max()
+        bound = 2 * 1000 * dUs[i] + 2 * 1000 * gm.dim * U_ROUND
+        assert err <= bound and perr <= bound, (i, gm.dim, err, perr, bound)
+
+
 def test_batched_equals_single_model_runs():
     specs = W.batched_chains(24, seed=5, dim_lo=32, dim_hi=640, n_steps=200)
     models, rhos = _setup(specs, "split_fp16x2")
@@ -123,6 +147,31 @@ def test_batched_equals_single_model_runs():
     for r, s_ in zip(rhos, singles):
         # same kernels; only the split-K slicing of the products differs
         assert (r - s_).abs().max().item() <= 1e-7
+
+
+def test_batched_autotune_keeps_parity():
+    """qed_autotune_batched times the GEMM1 tile widths on whole batched steps and stores the
+    fastest in the models; the next batched run (whatever width it uses) still matches the
+    oracle on instances with 128-column remainders."""
+    specs = W.batched_chains(8, seed=11, dim_lo=100, dim_hi=700, n_steps=150, record_every=50)
+    bases = [oracle.enumerate_basis(m) for m in specs]
+    refs = [oracle.evolve(m, n_steps=150, record_every=50, basis=b, obs_ids=list(range(b.dim)))
+            for m, b in zip(specs, bases)]
+    models, _ = _setup(specs, "split_fp16x2")
+    choice = qed.autotune_batched(models, steps=3)
+    print(choice)
+    assert choice.startswith("gemm1 ") and "256-wide" in choice and "128-wide" in choice
+    _, rhos = _setup(specs, "split_fp16x2")
+    recs = qed.evolve_batched(models, rhos, 150, record_every=50)
+    torch.cuda.synchronize()
+    for (rho_ref, rec_ref), r, rec in zip(refs, rhos, recs):
+        assert np.abs(r.cpu().numpy() - rho_ref).max() <= 1e-5
+        assert np.abs(rec.cpu().numpy() - rec_ref).max() <= 1e-6
+    with pytest.raises(qed.QedError):
+        qed.autotune_batched([models[0], models[0]])
+    m64, _ = _setup(specs[:1], "fp64")
+    with pytest.raises(qed.QedError):
+        qed.autotune_batched(m64)
 
 
 def test_batched_argument_errors():
