@@ -416,7 +416,7 @@ def make_roofline(kern, D, precision):
 
 def golden(name):
     path = os.path.join(ROOT, "tests", "golden", name)
-    return np.load(path) if os.path.exists(path) else None
+    return np.load(path) if name and os.path.isfile(path) else None
 
 
 def parity_against_golden(rho, records, qme_steps):

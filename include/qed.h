@@ -197,11 +197,21 @@ qed_status qed_set_scheme(qed_model *m, int32_t scheme);
  * have nothing to tune (OK).  EINVAL for steps <= 0. */
 qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choice_cap, qed_stream stream);
 
+/* Sets the tile plan that qed_autotune would otherwise choose (no counterpart in the paper):
+ * the tile width (128 or 256 columns) and split-K factor (CTAs per cluster, a power of two:
+ * GEMM1 up to 8, GEMM2 up to 4) of the step's two tensor-core products.  qed_evolve_batched
+ * takes the two widths for its grouped launches (unsplit) when every model of the batch
+ * carries the same ones.  Drops the captured step graphs; synchronises the device.  EINVAL
+ * for other values or for more slices than the product has 64-wide K blocks for (two per
+ * slice), EUNSUPPORTED for FP64 models. */
+qed_status qed_set_plan(qed_model *m, int32_t gemm1_bn, int32_t gemm1_splits, int32_t gemm2_bn, int32_t gemm2_splits,
+                        qed_stream stream);
+
 /* The batched counterpart (no counterpart in the paper either): the grouped launches of
  * qed_evolve_batched share one tile plan, so this times `steps` whole batched steps of the
- * n split-precision models `ms` for each GEMM1 tile width (256 and 128 columns; both
- * products unsplit, GEMM2 128-wide) and stores the fastest in every model; a later
- * qed_evolve_batched uses it when all its models carry the same width (else 256).  The
+ * n split-precision models `ms` for each pair of tile widths of the two products (GEMM1 256
+ * or 128 columns, GEMM2 128 or 256; both unsplit) and stores the fastest in every model; a
+ * later qed_evolve_batched uses it when all its models carry the same pair (else 256/256).  The
  * models' internal states are zeroed and used as scratch (qed_evolve_batched imports rho
  * again); synchronises the stream.  Writes the choice and the timings into `choice` (size
  * choice_cap; may be NULL).  EINVAL for n <= 0, steps <= 0, a NULL, repeated or FP64 model. */

@@ -81,6 +81,7 @@ def lib():
         "qed_set_scheme": [vp, i32],
         "qed_autotune": [vp, i32, ctypes.c_char_p, i32, vp],
         "qed_autotune_batched": [i32, ctypes.POINTER(vp), i32, ctypes.c_char_p, i32, vp],
+        "qed_set_plan": [vp, i32, i32, i32, i32, vp],
         "qed_evolve": [vp, vp, i64, i64, i32, i32, _c_int32_p, vp, vp],
         "qed_observables": [vp, vp, i32, _c_int32_p, vp, vp],
         "qed_sync_status": [vp, vp],
@@ -357,6 +358,11 @@ class Model:
 
     def set_renorm_every(self, every):
         _check(lib().qed_set_renorm_every(self._h, int(every)), "qed_set_renorm_every")
+
+    def set_plan(self, gemm1_bn, gemm1_splits, gemm2_bn, gemm2_splits, stream=None):
+        """Sets the tile widths and split-K factors of the step's two products (qed_set_plan)."""
+        _check(lib().qed_set_plan(self._h, int(gemm1_bn), int(gemm1_splits), int(gemm2_bn), int(gemm2_splits),
+                                  _stream_handle(stream)), "qed_set_plan")
 
     def autotune(self, steps=20, stream=None):
         """Times the step's tile widths and split-K factors (qed_autotune) and keeps the

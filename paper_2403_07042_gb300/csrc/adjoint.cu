@@ -463,6 +463,7 @@ qed_status make_twin(qed_model *m, cudaStream_t s) {
 // G = L_exp(X, M), X = -i dt H, contracted with dH/dtheta for every g and zeta.
 qed_status frechet_gradients(qed_model *m, Buffers &B, const double2 *Macc, double *grad_g, double *grad_zeta,
                              cudaStream_t s) {
+    NvtxRange range("adjoint: Frechet derivative and parameter gradients");
     AdjointState &a = *m->adj;
     const int64_t D = m->D;
     const size_t DD = (size_t)(D * D);
@@ -891,6 +892,7 @@ extern "C" qed_status qed_adjoint(qed_model *m, const void *rho0, int64_t n_step
         set_error("qed_adjoint: the effective-Hamiltonian step is not differentiated");
         return QED_EUNSUPPORTED;
     }
+    NvtxRange range("qed_adjoint");
     {
         // a failed set-up (e.g. out of device memory) leaves no half-built tables behind
         const qed_status st = setup(m);

@@ -269,6 +269,7 @@ int64_t next_multiple_after(int64_t off, int64_t i, int64_t every) {
 // jump operator of this library is a monomial, so A_j^+ A_j is diagonal), and
 // P_k = exp(-i H_kk dt - d_k dt/2).  Synchronises `s`.
 qed_status compute_propagator(qed_model *m, int scheme, cudaStream_t s) {
+    NvtxRange range("propagator (Pade-13 exp(-i H dt))");
     const int64_t D = m->D;
     const double dt = m->dt;
     const HostModel &hm = m->host;
@@ -420,6 +421,7 @@ qed_status qed_spec_restricted(const qed_spec *spec, const int64_t *keep, int64_
 }
 
 qed_status qed_build(const qed_spec *spec, double dt, qed_precision prec, qed_stream stream, qed_model **out) {
+    NvtxRange range("qed_build");
     if (!out) return einval("out is NULL");
     *out = nullptr;
     if (!(dt > 0.0) || !std::isfinite(dt)) return einval("dt must be finite and > 0");
@@ -486,6 +488,7 @@ qed_status qed_set_renorm_every(qed_model *m, int32_t every) {
 
 qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choice_cap, qed_stream stream) {
     if (!m || steps <= 0) return einval("qed_autotune: NULL model or steps <= 0");
+    NvtxRange range("qed_autotune");
     std::string c = "FP64 model: no tile choices";
     if (m->prec != QED_FP64) {
         // the captured step graphs hold the old step tables
@@ -505,6 +508,23 @@ qed_status qed_autotune(qed_model *m, int32_t steps, char *choice, int32_t choic
     return QED_OK;
 }
 
+qed_status qed_set_plan(qed_model *m, int32_t gemm1_bn, int32_t gemm1_splits, int32_t gemm2_bn, int32_t gemm2_splits,
+                        qed_stream stream) {
+    if (!m) return einval("qed_set_plan: NULL model");
+    if (m->prec == QED_FP64) {
+        set_error("qed_set_plan: FP64 models have no tile plan");
+        return QED_EUNSUPPORTED;
+    }
+    // the captured step graphs hold the old step tables
+    QED_CUDA_TRY(cudaDeviceSynchronize());
+    for (auto &g : m->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return split_set_plan(m, gemm1_bn, gemm1_splits, gemm2_bn, gemm2_splits, (cudaStream_t)stream);
+}
+
 qed_status qed_autotune_batched(int32_t n, qed_model *const *ms, int32_t steps, char *choice, int32_t choice_cap,
                                 qed_stream stream) {
     if (n <= 0 || !ms || steps <= 0) return einval("qed_autotune_batched: need n > 0 models and steps > 0");
@@ -514,6 +534,7 @@ qed_status qed_autotune_batched(int32_t n, qed_model *const *ms, int32_t steps, 
         for (int32_t j = 0; j < i; ++j)
             if (ms[j] == ms[i]) return einval("qed_autotune_batched: a model appears twice");
     }
+    NvtxRange range("qed_autotune_batched");
     std::string c;
     QED_TRY(split_autotune_batched(ms, n, (cudaStream_t)stream, steps, c));
     for (int32_t i = 0; i < n; ++i) QED_TRY(qed_sync_status(ms[i], stream));
@@ -585,6 +606,7 @@ qed_status qed_evolve(qed_model *m, void *rho_v, int64_t n_steps, int64_t step_o
     if (n_steps < 0 || step_offset < 0) return einval("negative step count");
     if (n_obs < 0) return einval("negative n_obs");
     if (n_obs > 0 && (record_every <= 0 || !records)) return einval("records need record_every > 0 and a buffer");
+    NvtxRange range("qed_evolve");
     cudaStream_t s = (cudaStream_t)stream;
     QED_TRY(ensure_ids(m, n_obs, obs_ids, s));
     double2 *rho = (double2 *)rho_v;
@@ -632,6 +654,7 @@ qed_status qed_evolve_batched(int32_t n, qed_model *const *ms, void *const *rhos
     if (n <= 0 || !ms || !rhos) return einval("qed_evolve_batched: need n > 0 models and rho pointers");
     if (n_steps < 0) return einval("qed_evolve_batched: negative step count");
     if (records && record_every <= 0) return einval("qed_evolve_batched: records need record_every > 0");
+    NvtxRange range("qed_evolve_batched");
     cudaStream_t s = (cudaStream_t)stream;
     const bool split = ms[0] && ms[0]->prec != QED_FP64;
     for (int32_t i = 0; i < n; ++i) {
@@ -750,6 +773,10 @@ qed_status qed_sync_status(qed_model *m, qed_stream stream) {
     if (e & kErrTimeout) { set_error("a bounded device wait ran out"); return QED_ETIMEOUT; }
     if (e & kErrNonFinite) { set_error("non-finite or non-positive trace at renormalisation"); return QED_ENUMERIC; }
     if (e & kErrSingular) { set_error("singular matrix"); return QED_ENUMERIC; }
+    if (e & kErrBounds) {
+        set_error("a device bounds check failed (QED_CHECKS build): an index read from a table was out of range");
+        return QED_ECUDA;
+    }
     if (e & kErrNotDensity) {
         set_error("split precision needs a Hermitian rho of unit trace (|rho_mn - conj(rho_nm)| <= 1e-8, "
                   "|tr rho - 1| <= 1e-6); that rho was evolved regardless and the result is not meaningful");
@@ -779,6 +806,7 @@ qed_status qed_select_states(qed_model *m, const void *rho0, int64_t steps_per_r
                              qed_stream stream) {
     if (!m || !rho0 || !out_model || !rho_out || !keep || !n_keep) return einval("NULL argument");
     if (steps_per_round <= 0 || n_rounds <= 0 || !(eps >= 0.0)) return einval("bad selection parameters");
+    NvtxRange range("qed_select_states");
     *out_model = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     using Owned = std::unique_ptr<qed_model, void (*)(qed_model *)>;

@@ -22,6 +22,7 @@
 #include <cuda_fp16.h>
 
 #include "df.h"
+#include "checks.h"
 #include "gemm_tc.h"
 #include "pdl.h"
 #include "kernels.h"
@@ -216,18 +217,24 @@ __host__ __device__ constexpr size_t ring_bytes() {
 constexpr size_t kPrefRho = 0, kPrefW = 32 * 64 * 16, kPrefWT = kPrefW + 2 * 32 * 64 * 4,
                  kPrefPm = kPrefWT + 2 * 64 * 32 * 4, kPrefPn = kPrefPm + 32 * 16, kPrefBytes = kPrefPn + 64 * 16;
 
+// The staged first chunk is kept for 128-wide kEpiV tiles only: a 256-wide one (large
+// products, long main loops) has no room for it beside its two 96 KB stages.
+template <int BN, int MODE>
+__host__ __device__ constexpr size_t pref_bytes_of() { return MODE == kEpiV && BN == 128 ? kPrefBytes : 0; }
+
 template <int BN, int MODE>
 __host__ __device__ constexpr size_t smem_bytes_of() {
-    return 1024 + ring_bytes<BN, MODE>() + (MODE == kEpiV ? kPrefBytes : 0) +
-           (2 * stages_of<BN, MODE>() + 1) * 8 + 32;
+    return 1024 + ring_bytes<BN, MODE>() + pref_bytes_of<BN, MODE>() + (2 * stages_of<BN, MODE>() + 1) * 8 + 32;
 }
 
 static_assert((size_t)4 * 32 * 36 * 4 <= ring_bytes<128, kEpiPlain>(), "plain epilogue tiles fit the ring");
 static_assert((size_t)kTcBM * tile_stride<128>() * 4 + 32 * 65 * (8 + 16) <= ring_bytes<128, kEpiV>(),
               "kEpiV buffers fit the ring");
+static_assert((size_t)kTcBM * tile_stride<256>() * 4 + 32 * 65 * (8 + 16) <= ring_bytes<256, kEpiV>(),
+              "kEpiV buffers fit the ring (256-wide)");
 static_assert((size_t)kTcBM * tile_stride<256>() * 4 <= ring_bytes<256, kEpiW>(), "kEpiW tile fits the ring");
 static_assert(smem_bytes_of<128, kEpiV>() <= 232448 && smem_bytes_of<128, kEpiW>() <= 232448 &&
-                  smem_bytes_of<256, kEpiW>() <= 232448,
+                  smem_bytes_of<256, kEpiW>() <= 232448 && smem_bytes_of<256, kEpiV>() <= 232448,
               "shared memory per CTA");
 
 // Threads of the cluster kernels: warps 0-3 run the pipeline roles and read the accumulator
@@ -282,6 +289,7 @@ __device__ __forceinline__ void epilogue_w(const Params &p, const uint32_t *peer
             x.z *= inv;
             x.w *= inv;
             const int64_t R = (int64_t)tile_m * kTcBM + r0 + base + u * rows_per_it + rsub;
+            if (!qed_check(p.err, R < 2 * Dp)) continue;
             const int64_t plane = R / Dp, k = R % Dp;
             *(float4 *)(w32 + plane * Dp * Dp + k * Dp + L) = x;
             const float a0 = x.x * s_w, a1 = x.y * s_w, a2 = x.z * s_w, a3 = x.w * s_w;
@@ -331,8 +339,8 @@ __device__ __forceinline__ void prefetch_v(const Params &p, uint32_t pref, int64
     cp_async_commit();
 }
 
-// One 32-row chunk (rows s0 .. s0 + 31 of the 128 x (64 complex) tile; m = 128 tile_m + row,
-// n = 64 tile_n + c):
+// One 32-row chunk of one 64-column group of the tile (rows s0 .. s0 + 31; m = 128 tile_m +
+// row, n = 64 tj + c, the group's [X_re | X_im] at columns coff .. coff + 127 of the tile):
 //   1. W(n, m) of the chunk transposed into shared memory,
 //   2. V_mn = P_m conj(P_n) (rho_mn + W_mn + conj(W_nm) + inv X_mn) for n >= m (lanes along
 //      n), written and kept in shared memory,
@@ -340,11 +348,11 @@ __device__ __forceinline__ void prefetch_v(const Params &p, uint32_t pref, int64
 // STAGED: rho, W and the phases come from the staged copy `pref`; otherwise from global
 // memory (with all of a thread's loads of a group in flight together).  `scratch` holds
 // [32][65] float2 and [32][65] float4.
-template <int NT, int S, bool STAGED>
-__device__ __forceinline__ void v_chunk(const Params &p, const uint32_t *peer, int s0, int tile_m, int tile_n,
+template <int NT, int S, bool STAGED, int BN>
+__device__ __forceinline__ void v_chunk(const Params &p, const uint32_t *peer, int s0, int tile_m, int tj, int coff,
                                         uint8_t *scratch, const uint8_t *pref) {
     static_assert(NT == 256, "the kEpiV thread mapping assumes 8 warps");
-    constexpr int TS = tile_stride<128>();
+    constexpr int TS = tile_stride<BN>();
     typedef float2 WRow[65];
     typedef float4 VRow[65];
     WRow *WTs = (WRow *)scratch;
@@ -361,7 +369,7 @@ __device__ __forceinline__ void v_chunk(const Params &p, const uint32_t *peer, i
     const float *pr_wt = (const float *)(pref + kPrefWT);
     const float4 *pr_pm = (const float4 *)(pref + kPrefPm);
     const float4 *pr_pn = (const float4 *)(pref + kPrefPn);
-    const int64_t m0 = (int64_t)tile_m * kTcBM, n0 = (int64_t)tile_n * 64;
+    const int64_t m0 = (int64_t)tile_m * kTcBM, n0 = (int64_t)tj * 64;
     const int t = threadIdx.x;
     {  // 1. W(n, m): lanes along m, 8 columns n per thread
         const int ml = t & 31, nb = t >> 5;
@@ -397,7 +405,7 @@ __device__ __forceinline__ void v_chunk(const Params &p, const uint32_t *peer, i
             const int ml = mr + 16 * pass;
             const int row = s0 + ml;
             const int64_t m = m0 + row;
-            const uint32_t off = (uint32_t)(row * TS + nq) * 4u;
+            const uint32_t off = (uint32_t)(row * TS + coff + nq) * 4u;
             float4 xr[S], xi[S];
 #pragma unroll
             for (int q = 0; q < S; ++q) {
@@ -489,7 +497,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *ring = smem;
     uint8_t *pref = smem + ring_bytes<BN, MODE>();
-    uint64_t *bars = (uint64_t *)(pref + (MODE == kEpiV ? kPrefBytes : 0));  // full[S], empty[S], accum
+    uint64_t *bars = (uint64_t *)(pref + pref_bytes_of<BN, MODE>());  // full[S], empty[S], accum
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * kTcStages + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     volatile int *issued = abort_flag + 1;    // TMA stage loads issued by the producer
@@ -498,7 +506,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // a 256-wide tile with 128 columns of the product left (the last tile when N is an odd
     // multiple of 128) computes only those
-    const bool narrow = BN == 256 && p.N - tile_n * BN <= BN / 2;
+    // (kEpiV: the tile's second 64-column group lies wholly past D)
+    const bool narrow = BN == 256 && (MODE == kEpiV ? (int64_t)(2 * tile_n + 1) * 64 >= p.epi.D
+                                                    : p.N - tile_n * BN <= BN / 2);
     const int kb0 = split * p.kb_per_split;
     const int nkb = min(p.kb_per_split, p.kb_total - kb0);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages),
@@ -552,7 +562,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
 
     constexpr int rows = kTcBM / S;
     const int r0 = split * rows;
-    if constexpr (MODE == kEpiV) {
+    if constexpr (MODE == kEpiV && BN == 128) {
         if (warp >= 2) prefetch_v<NT>(p, smem_u32(pref), (int64_t)tile_m * kTcBM + r0, (int64_t)tile_n * 64, 64);
     }
 
@@ -697,7 +707,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
                     dst[q] = __uint_as_float(mv[q]) + (corr ? __uint_as_float(cv[q]) : 0.f);
             }
         }
-        if constexpr (MODE == kEpiV) {
+        if constexpr (MODE == kEpiV && BN == 128) {
             if (warp >= 2) cp_async_wait_all();  // the staged inputs of the first chunk
         }
         __syncwarp();
@@ -709,9 +719,23 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap *tmA, const CUtensor
             epilogue_w<BN, NT, S>(p, peer, r0, tile_m, tile_n);
         } else {
             uint8_t *scratch = (uint8_t *)(tile + kTcBM * TS);
-            v_chunk<NT, S, true>(p, peer, r0, tile_m, tile_n, scratch, pref);
+            if constexpr (BN == 128) {
+                v_chunk<NT, S, true, BN>(p, peer, r0, tile_m, tile_n, 0, scratch, pref);
 #pragma unroll 1
-            for (int s0 = r0 + 32; s0 < r0 + rows; s0 += 32) v_chunk<NT, S, false>(p, peer, s0, tile_m, tile_n, scratch, pref);
+                for (int s0 = r0 + 32; s0 < r0 + rows; s0 += 32)
+                    v_chunk<NT, S, false, BN>(p, peer, s0, tile_m, tile_n, 0, scratch, pref);
+            } else {
+                // the tile's 64-column groups one after another (B's rows hold [re | im] of 64
+                // columns per 128 rows); groups wholly past D are padding
+#pragma unroll 1
+                for (int g = 0; g < BN / 128; ++g) {
+                    const int tj = (BN / 128) * tile_n + g;
+                    if ((int64_t)tj * 64 >= p.epi.D) break;
+#pragma unroll 1
+                    for (int s0 = r0; s0 < r0 + rows; s0 += 32)
+                        v_chunk<NT, S, false, BN>(p, peer, s0, tile_m, tj, 128 * g, scratch, pref);
+                }
+            }
         }
         __syncwarp();
         cluster_sync();  // no CTA leaves while a peer may still read its tile
@@ -809,12 +833,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1) tc_gemm_single_kernel(cons
         const int tmv = t / tl.ntn;
         tm = (tmv / tl.nmp) * tl.dpt + tmv % tl.nmp;
     } else {
+        // rows of tiles on or above the diagonal: row tm holds the tiles from column tile
+        // 2 tm / c (c = 64-column groups per tile) to the last holding columns < D
+        constexpr int c = BN / 128;
+        const int ntt = (tl.ntj + c - 1) / c;
         tm = 0;
-        while (t >= tl.ntj - 2 * tm) {  // rows of tiles on or above the diagonal
-            t -= tl.ntj - 2 * tm;
+        while (t >= ntt - 2 * tm / c) {
+            t -= ntt - 2 * tm / c;
             ++tm;
         }
-        tn = 2 * tm + t;
+        tn = 2 * tm / c + t;
     }
     gemm_tile<BN, kClusterThreads, MODE, S>(&tmA, &tmB, p, tm, tn, split);
 }
@@ -940,7 +968,11 @@ bool tc_gemm_prepare_grouped() {
         !set_smem(tc_gemm_single_kernel<256, kEpiW, 8>, smem_bytes_of<256, kEpiW>()) ||
         !set_smem(tc_gemm_single_kernel<128, kEpiV, 1>, smem_bytes_of<128, kEpiV>()) ||
         !set_smem(tc_gemm_single_kernel<128, kEpiV, 2>, smem_bytes_of<128, kEpiV>()) ||
-        !set_smem(tc_gemm_single_kernel<128, kEpiV, 4>, smem_bytes_of<128, kEpiV>()))
+        !set_smem(tc_gemm_single_kernel<128, kEpiV, 4>, smem_bytes_of<128, kEpiV>()) ||
+        !set_smem(tc_gemm_grouped_kernel<256, kEpiV>, smem_bytes_of<256, kEpiV>()) ||
+        !set_smem(tc_gemm_single_kernel<256, kEpiV, 1>, smem_bytes_of<256, kEpiV>()) ||
+        !set_smem(tc_gemm_single_kernel<256, kEpiV, 2>, smem_bytes_of<256, kEpiV>()) ||
+        !set_smem(tc_gemm_single_kernel<256, kEpiV, 4>, smem_bytes_of<256, kEpiV>()))
         return false;
     done = true;
     return true;
@@ -950,12 +982,14 @@ cudaError_t tc_gemm_grouped_launch(const GemmItem *items, int n_items, const Gem
                                    int bn, int mode, int cluster, uint32_t *err, cudaStream_t s) {
     if (n_items <= 0) return cudaSuccess;
     // the grouped form runs every product unsplit (each instance of a batch is one job)
-    if (cluster != 1 || (mode != kEpiW && mode != kEpiV) || (mode == kEpiV && bn != 128))
-        return cudaErrorInvalidValue;
+    if (cluster != 1 || (mode != kEpiW && mode != kEpiV) || (bn != 128 && bn != 256)) return cudaErrorInvalidValue;
     count_launches(1);
     const dim3 grid(n_items), block(kClusterThreads);
-    if (mode == kEpiV)
+    if (mode == kEpiV && bn == 128)
         return launch_pdl(tc_gemm_grouped_kernel<128, kEpiV>, grid, block, smem_bytes_of<128, kEpiV>(), s, items, jobs,
+                          segs, err);
+    if (mode == kEpiV)
+        return launch_pdl(tc_gemm_grouped_kernel<256, kEpiV>, grid, block, smem_bytes_of<256, kEpiV>(), s, items, jobs,
                           segs, err);
     if (bn == 128)
         return launch_pdl(tc_gemm_grouped_kernel<128, kEpiW>, grid, block, smem_bytes_of<128, kEpiW>(), s, items, jobs,
@@ -987,7 +1021,8 @@ int tc_gemm_single_ctas(const TcGemm &g, int mode, int64_t D) {
     if (mode == kEpiW) {
         tiles = 2 * t.nmp * t.ntn;
     } else {
-        for (int tm = 0; tm < t.nmp; ++tm) tiles += t.ntj - 2 * tm;
+        const int c = g.bn / 128, ntt = (t.ntj + c - 1) / c;
+        for (int tm = 0; tm < t.nmp; ++tm) tiles += ntt - 2 * tm / c;
     }
     return tiles * g.splits;
 }
@@ -1007,11 +1042,18 @@ cudaError_t tc_gemm_single_launch(const TcGemm &g, const GemmJob &job, const TcS
     const SingleTiles t = single_tiles(g, mode, D);
     count_launches(1);
     if (mode == kEpiV) {
-        if (g.bn != 128) return cudaErrorInvalidValue;
+        if (g.bn == 128) {
+            switch (g.splits) {
+                case 1: return single_launch<128, kEpiV, 1>(g, p, t, ctas, s);
+                case 2: return single_launch<128, kEpiV, 2>(g, p, t, ctas, s);
+                case 4: return single_launch<128, kEpiV, 4>(g, p, t, ctas, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
         switch (g.splits) {
-            case 1: return single_launch<128, kEpiV, 1>(g, p, t, ctas, s);
-            case 2: return single_launch<128, kEpiV, 2>(g, p, t, ctas, s);
-            case 4: return single_launch<128, kEpiV, 4>(g, p, t, ctas, s);
+            case 1: return single_launch<256, kEpiV, 1>(g, p, t, ctas, s);
+            case 2: return single_launch<256, kEpiV, 2>(g, p, t, ctas, s);
+            case 4: return single_launch<256, kEpiV, 4>(g, p, t, ctas, s);
             default: return cudaErrorInvalidValue;
         }
     }

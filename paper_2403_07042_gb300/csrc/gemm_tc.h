@@ -57,9 +57,10 @@ cudaError_t tc_gemm_launch(const TcGemm &g, float *out, uint32_t *err, cudaStrea
 //     shared memory (fixed order) and each CTA of the cluster writes its share of rows: W
 //     (FP32 [2][Dp][Dp], scaled by inv) and the FP16 hi/lo planes of GEMM2's A operand
 //     (rows k = [W_re | W_im], scaled by s_w).
-//   kEpiV (GEMM2, 128-wide tiles only): B's rows are ordered so that tile column group g
-//     holds [X_re | X_im] of the 64 complex columns 64g..64g+63.  Only tiles on or above the
-//     diagonal are launched (X and V are Hermitian).  After the same cluster reduction each
+//   kEpiV (GEMM2): B's rows are ordered so that every 128 rows hold [X_re | X_im] of 64
+//     complex columns (64g..64g+63 for the g-th 128 rows); a tile covers one such group
+//     (128-wide) or two (256-wide).  Only tiles on or above the diagonal are launched (X and
+//     V are Hermitian).  After the same cluster reduction each
 //     CTA forms, for its rows m and the tile's columns n >= m,
 //       V_mn = P_m conj(P_n) (rho_mn + W_mn + conj(W_nm) + inv X_mn)
 //     in double-float (U rho U^+ in the increment form) and writes V_mn and V_nm = conj(V_mn).
@@ -109,7 +110,7 @@ struct TcSegs {
 
 bool tc_gemm_prepare_grouped();
 // All jobs of one launch share the epilogue mode (kEpiW or kEpiV), the tile width bn (128
-// or 256; kEpiV needs 128) and the cluster size (equal to the jobs' splits).  Returns the
+// or 256) and the cluster size (equal to the jobs' splits).  Returns the
 // launch status.
 cudaError_t tc_gemm_grouped_launch(const GemmItem *items, int n_items, const GemmJob *jobs, const TcSegs &segs,
                                    int bn, int mode, int cluster, uint32_t *err, cudaStream_t s);
@@ -118,7 +119,8 @@ cudaError_t tc_gemm_grouped_launch(const GemmItem *items, int n_items, const Gem
 // parameters (nothing read from tables before the first TMA load).  The work items are the
 // same as the grouped form's for that model: kEpiW skips the tiles that lie wholly in the
 // zero padding (rows of a plane or columns >= D), kEpiV runs the tiles on or above the
-// diagonal (128 rows x 64 complex columns), each as g.splits consecutive CTAs (a cluster).
+// diagonal (128 rows x 64 or 128 complex columns), each as g.splits consecutive CTAs (a
+// cluster).
 cudaError_t tc_gemm_single_launch(const TcGemm &g, const GemmJob &job, const TcSegs &segs, int64_t D,
                                   uint32_t *err, cudaStream_t s);
 // Bytes one pipeline stage of a product in `mode` receives (kEpiW / kEpiV stages hold every

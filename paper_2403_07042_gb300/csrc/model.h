@@ -7,12 +7,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "builder.h"
 #include "qed.h"
 
 struct qed_model;
 
 namespace qed {
+
+// A named range on the host timeline (NVTX) around a phase of the library's work: shown by
+// timeline profilers, a no-op unless one is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 void set_error(const std::string &msg);
 
@@ -35,6 +46,7 @@ enum : uint32_t {
     kErrSingular = 2u,
     kErrTimeout = 4u,
     kErrNotDensity = 8u,   // split precision given a rho that is not Hermitian with unit trace
+    kErrBounds = 16u,      // a device bounds check of the QED_CHECKS build failed
 };
 
 // Tolerances of that check (absolute): max |rho_mn - conj(rho_nm)| and |tr rho - 1|.

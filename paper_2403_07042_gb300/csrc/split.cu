@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "checks.h"
 #include "gemm_tc.h"
 #include "kernels.h"
 #include "pdl.h"
@@ -47,6 +48,7 @@ struct InstDesc {
     const int4 *jtab;       // [D][kInMax] per jump j < nj: {src or -1, coef hi, coef lo, 0}, or null
     int nj;
     __half *rho_pl;
+    uint32_t *err;          // the instance's error word (bounds checks of the QED_CHECKS build)
 };
 
 // Rows with at most kInMax incoming jump entries use a padded table (one vector load per
@@ -71,9 +73,10 @@ struct Batch {
     int n_items1 = 0, n_items2 = 0;
     TileItem *etiles = nullptr;
     int n_etiles = 0;
+    bool jt = false;  // every instance has per-jump incoming tables (dissipate_jt_kernel)
     int cs1 = 1, cs2 = 1;  // split-K slices of GEMM1 / GEMM2 = CTAs per cluster
     int scheme = QED_SCHEME_LIE;
-    int bn1 = 256, bn2 = 128;  // tile widths (one per grouped launch; GEMM2's is 128)
+    int bn1 = 256, bn2 = 128;  // tile widths (one per grouped launch)
     // one model on its own: its products launch with their tensor maps and jobs as kernel
     // parameters (tc_gemm_single_launch) instead of through the tables above
     bool single = false;
@@ -109,7 +112,7 @@ struct SplitState {
     int4 *jtab = nullptr;                    // per-jump incoming table (at most kInMax jumps)
     int nj = 0;
     double scale_delta = 1.0, scale_rho = 1.0, scale_w = 1.0;
-    int batch_bn1 = kTcBNMax;  // GEMM1 tile width of the grouped launches (qed_autotune_batched)
+    int batch_bn1 = kTcBNMax, batch_bn2 = kTcBNMax;  // tile widths of the grouped launches (qed_autotune_batched)
 };
 
 namespace {
@@ -271,7 +274,7 @@ __device__ __forceinline__ float4 *state_buf(const InstDesc &a, int sel) {
 // longer one by bisection; the owner lane gets the sum of c_p c_q X[src_p, src_q] (dt
 // included in the coefficients) added to (gr, gi).  Returns whether this lane's own pair
 // was handled.  Kept out of line so that the common path keeps its registers.
-__device__ __noinline__ bool long_merge_df(int64_t D, const int32_t *in_jump, const int32_t *in_src,
+__device__ __noinline__ bool long_merge_df(uint32_t *err, int64_t D, const int32_t *in_jump, const int32_t *in_src,
                                            const float2 *coef, const float4 *X, int p, int pe, int q, int qe,
                                            float &gr, float &gi) {
     const bool is_long = pe > p && qe > q && (pe - p) + (qe - q) > kLongMerge;
@@ -296,8 +299,9 @@ __device__ __noinline__ bool long_merge_df(int64_t D, const int32_t *in_jump, co
                 else
                     hi = mid;
             }
-            if (lo < l1 && in_jump[lo] == j) {
-                const int ep = m_short ? e : lo, eq = m_short ? lo : e;  // row m's entry, row n's
+            const int ep = m_short ? e : lo, eq = m_short ? lo : e;  // row m's entry, row n's
+            if (lo < l1 && in_jump[lo] == j &&
+                qed_check(err, in_src[ep] >= 0 && in_src[ep] < D && in_src[eq] >= 0 && in_src[eq] < D)) {
                 const float2 cp = coef[ep], cq = coef[eq];
                 const df c = df_mul({cp.x, cp.y}, {cq.x, cq.y});
                 const float4 u = X[(int64_t)in_src[ep] * D + in_src[eq]];
@@ -396,7 +400,8 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
             v[r] = X[(inside ? m : 0) * D + nc];
 #pragma unroll
             for (int j = 0; j < kInMax; ++j) {
-                const bool hit = inside && tm[r][j].x >= 0 && tn[j].x >= 0;
+                const bool hit = inside && tm[r][j].x >= 0 && tn[j].x >= 0 &&
+                                 qed_check(a.err, tm[r][j].x < D && tn[j].x < D);
                 u[r][j] = hit ? X[(int64_t)tm[r][j].x * D + tn[j].x] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -458,7 +463,8 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
                         src = en[j].y;
                         c2 = make_float2(__int_as_float(en[j].z), __int_as_float(en[j].w));
                     }
-                hit[r][i] = h && em[r][i].x != kNoJump && inside;
+                hit[r][i] = h && em[r][i].x != kNoJump && inside &&
+                            qed_check(a.err, em[r][i].y >= 0 && em[r][i].y < D && src >= 0 && src < D);
                 cq[r][i] = c2;
                 u[r][i] = hit[r][i] ? X[(int64_t)em[r][i].y * D + src] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -500,7 +506,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
         int p = inside ? a.in_ptr[m] : 0, pe = inside ? a.in_ptr[m + 1] : 0;
         int q = inside ? a.in_ptr[n] : 0, qe = inside ? a.in_ptr[n + 1] : 0;
         // long lists: merged by the whole warp
-        const bool is_long = long_merge_df(D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
+        const bool is_long = long_merge_df(a.err, D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
         if (is_long) pe = p;  // done: skip the serial merge
         while (p < pe && q < qe) {  // jumps present in both incoming lists
             const int jp = a.in_jump[p], jq = a.in_jump[q];
@@ -508,7 +514,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
                 ++p;
             } else if (jp > jq) {
                 ++q;
-            } else {
+            } else if (qed_check(a.err, a.in_src[p] >= 0 && a.in_src[p] < D && a.in_src[q] >= 0 && a.in_src[q] < D)) {
                 const float2 cp = a.coef[p], cqq = a.coef[q];
                 const df c = df_mul({cp.x, cp.y}, {cqq.x, cqq.y});  // dt c_j(m) c_j(n)
                 const float4 uu = X[(int64_t)a.in_src[p] * D + a.in_src[q]];
@@ -522,6 +528,89 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
         if (!inside) continue;
         const cdf b = LIE ? v : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
         lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
+    }
+}
+
+// The Lie step's update (rho = V + dt L(V) and the next planes) for instances whose incoming
+// entries are all in per-jump tables (at most kInMax jumps of monomial form).  The block's
+// row and column entries and damping rates are staged in shared memory first, so a thread
+// keeps only its kRows elements' loads in registers; with 64 registers four blocks fit on an
+// SM, and a dim-512 update (512 blocks) runs as one wave whose table reads overlap the
+// previous kernel.
+__global__ void __launch_bounds__(256, 4) dissipate_jt_kernel(const TileItem *__restrict__ tiles,
+                                                           const InstDesc *__restrict__ descs) {
+    constexpr int R = 8 * kRows;
+    constexpr int JW = kInMax;
+    __shared__ int4 s_row[R][JW], s_col[32][JW];
+    __shared__ float2 s_dr[R], s_dc[32];
+    const TileItem it = tiles[blockIdx.x];
+    const InstDesc a = descs[it.inst];
+    // element offsets in 32 bits: the split path holds dimensions below 65536 (split_create)
+    const uint32_t D = (uint32_t)a.D;
+    const int nj = a.nj;
+    const uint32_t n0 = (uint32_t)it.bx * 32, m0 = (uint32_t)it.by * R;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    // entries: the block's R rows, then its 32 columns, then both damping vectors
+    for (int e = tid; e < (R + 32) * JW + R + 32; e += 256) {
+        if (e < R * JW) {
+            const int r = e / JW, j = e % JW;
+            const uint32_t m = m0 + r;
+            s_row[r][j] = j < nj && m < D ? a.jtab[m * JW + j] : make_int4(-1, 0, 0, 0);
+        } else if (e < (R + 32) * JW) {
+            const int c = (e - R * JW) / JW, j = e % JW;
+            const uint32_t n = n0 + c;
+            s_col[c][j] = j < nj && n < D ? a.jtab[n * JW + j] : make_int4(-1, 0, 0, 0);
+        } else if (e < (R + 32) * JW + R) {
+            const int r = e - (R + 32) * JW;
+            s_dr[r] = m0 + r < D ? a.damp[m0 + r] : make_float2(0.f, 0.f);
+        } else {
+            const int c = e - (R + 32) * JW - R;
+            s_dc[c] = n0 + c < D ? a.damp[n0 + c] : make_float2(0.f, 0.f);
+        }
+    }
+    const float4 *X = a.V;
+    float4 *O = a.rho;
+    __syncthreads();
+    pdl_wait();
+    pdl_trigger();
+    const int tx = threadIdx.x;
+    const uint32_t n = n0 + tx;
+    // the jump terms are formed in FP32 (their size is dt gamma of the result), so each
+    // gathered element contributes only the leading words of its real and imaginary parts
+    float4 v[kRows];
+    float ur[kRows][JW], ui[kRows][JW];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int rr = threadIdx.y + 8 * r;
+        const uint32_t m = m0 + rr;
+        const bool inside = m < D && n < D;
+        v[r] = inside ? X[m * D + n] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < JW; ++j) {
+            const int sm = s_row[rr][j].x, sn = s_col[tx][j].x;
+            const bool hit = inside && sm >= 0 && sn >= 0 && qed_check(a.err, (uint32_t)sm < D && (uint32_t)sn < D);
+            const float *src = (const float *)(X + ((uint32_t)sm * D + (uint32_t)sn));
+            ur[r][j] = hit ? src[0] : 0.f;
+            ui[r][j] = hit ? src[2] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int rr = threadIdx.y + 8 * r;
+        const uint32_t m = m0 + rr;
+        if (!(m < D && n < D)) continue;
+        const cdf vv = load_cdf(v[r]);
+        float gr, gi;
+        damping_term(s_dr[rr], s_dc[tx], vv, gr, gi);
+#pragma unroll
+        for (int j = 0; j < JW; ++j) {
+            const int4 em = s_row[rr][j], en = s_col[tx][j];
+            if (!(em.x >= 0 && en.x >= 0)) continue;
+            const df c = df_mul({__int_as_float(em.y), __int_as_float(em.z)}, {__int_as_float(en.y), __int_as_float(en.z)});
+            gr = __fmaf_rn(c.hi, ur[r][j], __fmaf_rn(c.lo, ur[r][j], gr));
+            gi = __fmaf_rn(c.hi, ui[r][j], __fmaf_rn(c.lo, ui[r][j], gi));
+        }
+        lindblad_store<true>(a, O, m, n, vv, 1.f, gr, gi, true);
     }
 }
 
@@ -661,12 +750,13 @@ qed_status upload(T **dst, const std::vector<T> &v) {
 }
 
 // The plans of a model's two products: GEMM1 [W_re; W_im] = A1 . rho^T (2Dp x Dp, K 2Dp, four
-// plane pairs), GEMM2 [X_re | X_im] = W . B2^T (Dp x 2Dp, K 2Dp, three plane pairs) with
-// 128-wide tiles.  splits = CTAs per cluster (on-chip reduction of the split-K slices).
-bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, int splits2) {
+// plane pairs), GEMM2 [X_re | X_im] = W . B2^T (Dp x 2Dp, K 2Dp, three plane pairs).  Widths and
+// splits = CTAs per cluster (on-chip reduction of the split-K slices) as given, or 0 for the
+// planner's rule (256-wide tiles once they fill half the SMs).
+bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, int splits2, int bn2 = 0) {
     const int Dp = (int)S.Dp;
     return tc_gemm_plan(g1, S.a1, 3, S.rho_pl, 2, 2 * Dp, Dp, 2 * Dp, 4, kSeg1Pairs, S.num_sms, splits1, bn1, true) &&
-           tc_gemm_plan(g2, S.w_pl, 2, S.b2, 3, Dp, 2 * Dp, 2 * Dp, 3, kSeg2Pairs, S.num_sms, splits2, 128, true);
+           tc_gemm_plan(g2, S.w_pl, 2, S.b2, 3, Dp, 2 * Dp, 2 * Dp, 3, kSeg2Pairs, S.num_sms, splits2, bn2, true);
 }
 
 // Descriptors, jobs and work lists of a batch.  With `single` set (one model on its own)
@@ -674,7 +764,8 @@ bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, 
 // product runs unsplit, largest first, since the batch itself fills the GPU.  GEMM1 skips
 // tiles that lie wholly in the zero padding (rows or columns >= D); GEMM2 runs the tiles on
 // or above the diagonal only (its epilogue writes both halves of the Hermitian V).
-qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int batch_bn1 = kTcBNMax) {
+qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int batch_bn1 = kTcBNMax,
+                       int batch_bn2 = kTcBNMax) {
     b.release();
     b.n = n;
     b.scheme = ms[0]->scheme;
@@ -709,11 +800,12 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int b
         d.jtab = S.jtab;
         d.nj = S.nj;
         d.rho_pl = S.rho_pl;
+        d.err = m->err;
         TcGemm bg1 = S.g1, bg2 = S.g2;
-        if (!single && !plan_products(S, bg1, bg2, 1, batch_bn1, 1)) return QED_ECUDA;
+        if (!single && !plan_products(S, bg1, bg2, 1, batch_bn1, 1, batch_bn2)) return QED_ECUDA;
         auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
         if (!pow2(bg1.splits) || bg1.splits > kTcMaxCluster || !pow2(bg2.splits) || bg2.splits > kTcMaxClusterV ||
-            bg2.bn != 128) {
+            (bg2.bn != 128 && bg2.bn != 256)) {
             set_error("split step: product plan outside the cluster epilogue's limits");
             return QED_EINVAL;
         }
@@ -765,11 +857,12 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int b
                 for (int sp = 0; sp < bg1.splits; ++sp) it1.push_back({i, tm, tn, sp});
             }
         }
-        // GEMM2 tiles: 128 rows m x 64 complex columns n, on or above the diagonal
+        // GEMM2 tiles: 128 rows m x (64 c2) complex columns n, on or above the diagonal
+        const int c2 = bg2.bn / 128;
         for (int tm = 0; tm < bg2.M / kTcBM; ++tm) {
             if ((int64_t)tm * kTcBM >= D) continue;
-            for (int tj = 2 * tm; tj < bg2.N / 128; ++tj) {
-                if ((int64_t)tj * 64 >= D) continue;
+            for (int tj = 2 * tm / c2; tj < bg2.N / bg2.bn; ++tj) {
+                if ((int64_t)tj * 64 * c2 >= D) continue;
                 for (int sp = 0; sp < bg2.splits; ++sp) it2.push_back({i, tm, tj, sp});
             }
         }
@@ -801,6 +894,7 @@ qed_status build_batch(Batch &b, qed_model *const *ms, int n, bool single, int b
     b.n_items1 = (int)it1.size();
     b.n_items2 = (int)it2.size();
     b.n_etiles = (int)et.size();
+    b.jt = std::all_of(desc.begin(), desc.end(), [](const InstDesc &d) { return d.jtab != nullptr; });
     if (single) {
         SplitState &S = *ms[0]->sp;
         b.single = true;
@@ -832,7 +926,8 @@ void launch_gemm2(const Batch &b, uint32_t *err, cudaStream_t s) {
         tc_gemm_grouped_launch(b.items2, b.n_items2, b.jobs2, kSegs2, b.bn2, kEpiV, b.cs2, err, s);
 }
 void launch_dissipate(const Batch &b, cudaStream_t s) {
-    launch_pdl(dissipate_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles, b.desc);
+    launch_pdl(b.jt ? dissipate_jt_kernel : dissipate_df_kernel, dim3(b.n_etiles), dim3(32, 8), 0, s, b.etiles,
+               b.desc);
     count_launches(1);
 }
 void launch_lindblad(const Batch &b, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s) {
@@ -855,6 +950,11 @@ qed_status split_prepare(qed_model *m, cudaStream_t s) {
     const int64_t D = m->D;
     const int64_t Dp = (D + kTcBM - 1) / kTcBM * kTcBM;
     const size_t W2 = (size_t)(2 * Dp) * (size_t)(2 * Dp);
+    if (D >= 65536) {
+        // (its buffers would exceed any device's memory; the Lindblad kernels index in 32 bits)
+        set_error("split precision: dimensions up to 65535");
+        return QED_EINVAL;
+    }
     if (!m->sp) {
         m->sp = new SplitState();
         SplitState &S = *m->sp;
@@ -1016,8 +1116,8 @@ void split_step(qed_model *m, cudaStream_t s) { batch_step(m->sp->self, m->err, 
 
 // Chooses the tile width and split-K factor (CTAs per cluster) of each of the model's two
 // products by timing whole steps: GEMM1's candidates (128- and 256-wide tiles, 1, 2, 4 or 8
-// slices) with GEMM2 as planned, then GEMM2's (128-wide, 1, 2 or 4 slices) with the best
-// GEMM1.  Plans whose slices would not be a power of two are skipped.  Overwrites the
+// slices) with GEMM2 as planned, then GEMM2's (128- and 256-wide, 1, 2 or 4 slices) with the
+// best GEMM1.  Plans whose slices would not be a power of two are skipped.  Overwrites the
 // internal state (qed_evolve imports rho again) and replaces the step tables; the caller
 // drops its captured graphs.
 qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &choice) {
@@ -1025,12 +1125,11 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
     qed_model *self[1] = {m};
     auto candidates = [&](int which, std::vector<TcGemm> &out) -> qed_status {
         for (int bn : {128, 256}) {
-            if (which == 2 && bn != 128) continue;
             for (int sp : {1, 2, 4, 8}) {
                 if (which == 2 && sp > kTcMaxClusterV) continue;
                 TcGemm g1, g2;
                 if (!plan_products(S, g1, g2, which == 1 ? sp : S.g1.splits, which == 1 ? bn : S.g1.bn,
-                                   which == 2 ? sp : S.g2.splits))
+                                   which == 2 ? sp : S.g2.splits, which == 2 ? bn : S.g2.bn))
                     return QED_ECUDA;
                 const TcGemm &g = which == 1 ? g1 : g2;
                 bool seen = (g.splits & (g.splits - 1)) != 0;
@@ -1088,8 +1187,9 @@ qed_status split_autotune(qed_model *m, cudaStream_t s, int steps, std::string &
 }
 
 // The batched counterpart: the grouped launches share one plan, so the candidates are the
-// tile widths of GEMM1 (128, 256; unsplit, GEMM2 128-wide), each timed on `steps` whole
-// batched steps from a zero state.  The winner is kept in every model of the batch.
+// tile widths of the two products (GEMM1 256 or 128, GEMM2 128 or 256; both unsplit), each
+// pair timed on `steps` whole batched steps from a zero state.  The winner is kept in every
+// model of the batch.
 qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, int steps, std::string &choice) {
     for (int i = 0; i < n; ++i) {
         SplitState &S = *ms[i]->sp;
@@ -1102,15 +1202,16 @@ qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, i
     Batch b;
     qed_status st = QED_OK;
     float best = -1.f;
-    int best_bn = kTcBNMax;
+    int best1 = kTcBNMax, best2 = kTcBNMax;
     std::string times;
-    for (int bn : {256, 128}) {
+    const int plans[4][2] = {{256, 256}, {128, 256}, {256, 128}, {128, 128}};
+    for (const auto &pl : plans) {
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             set_error(std::string("autotune (batched): ") + cudaGetErrorString(cudaGetLastError()));
             st = QED_ECUDA;
             break;
         }
-        if ((st = build_batch(b, ms, n, false, bn)) != QED_OK) break;
+        if ((st = build_batch(b, ms, n, false, pl[0], pl[1])) != QED_OK) break;
         for (int i = 0; i < 2; ++i) batch_step(b, ms[0]->err, s);
         float t = 0.f;
         if (cudaEventRecord(e0, s) != cudaSuccess) { st = QED_ECUDA; break; }
@@ -1121,18 +1222,40 @@ qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, i
             st = QED_ECUDA;
             break;
         }
-        times += (times.empty() ? "" : ", ") + std::to_string(bn) + "-wide " + std::to_string(1e3 * t / steps) +
-                 " us";
-        if (best < 0.f || t < best) best = t, best_bn = bn;
+        times += (times.empty() ? "" : ", ") + std::to_string(pl[0]) + "/" + std::to_string(pl[1]) + " " +
+                 std::to_string(1e3 * t / steps) + " us";
+        if (best < 0.f || t < best) best = t, best1 = pl[0], best2 = pl[1];
     }
     cudaStreamSynchronize(s);
     b.release();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != QED_OK) return st;
-    for (int i = 0; i < n; ++i) ms[i]->sp->batch_bn1 = best_bn;
-    choice = "gemm1 " + std::to_string(best_bn) + "-wide (batched step: " + times + ")";
+    for (int i = 0; i < n; ++i) ms[i]->sp->batch_bn1 = best1, ms[i]->sp->batch_bn2 = best2;
+    choice = "gemm1 " + std::to_string(best1) + "-wide, gemm2 " + std::to_string(best2) +
+             "-wide (batched step, gemm1/gemm2 widths: " + times + ")";
     return QED_OK;
+}
+
+qed_status split_set_plan(qed_model *m, int bn1, int splits1, int bn2, int splits2, cudaStream_t s) {
+    SplitState &S = *m->sp;
+    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+    if ((bn1 != 128 && bn1 != 256) || (bn2 != 128 && bn2 != 256) || !pow2(splits1) || splits1 > kTcMaxCluster ||
+        !pow2(splits2) || splits2 > kTcMaxClusterV) {
+        set_error("qed_set_plan: widths 128 or 256, slices a power of two (GEMM1 <= 8, GEMM2 <= 4)");
+        return QED_EINVAL;
+    }
+    TcGemm g1, g2;
+    if (!plan_products(S, g1, g2, splits1, bn1, splits2, bn2)) return QED_ECUDA;
+    if (g1.splits != splits1 || g2.splits != splits2) {
+        set_error("qed_set_plan: more K slices than the product's 64-wide K blocks allow");
+        return QED_EINVAL;
+    }
+    S.g1 = g1;
+    S.g2 = g2;
+    S.batch_bn1 = bn1;
+    S.batch_bn2 = bn2;
+    return split_rebuild(m, s);
 }
 
 void split_lindblad_stage(qed_model *m, int xsel, int bsel, int osel, float f, int planes, cudaStream_t s) {
@@ -1229,11 +1352,11 @@ void split_populations(qed_model *m, double *out, cudaStream_t s) {
 
 qed_status split_batch_create(qed_model *const *ms, int n, Batch **out) {
     Batch *b = new Batch();
-    // the tuned tile width when every model of the batch carries the same one
-    int bn1 = ms[0]->sp->batch_bn1;
+    // the tuned tile widths when every model of the batch carries the same ones
+    int bn1 = ms[0]->sp->batch_bn1, bn2 = ms[0]->sp->batch_bn2;
     for (int i = 1; i < n; ++i)
-        if (ms[i]->sp->batch_bn1 != bn1) bn1 = kTcBNMax;
-    qed_status st = build_batch(*b, ms, n, false, bn1);
+        if (ms[i]->sp->batch_bn1 != bn1 || ms[i]->sp->batch_bn2 != bn2) bn1 = kTcBNMax, bn2 = kTcBNMax;
+    qed_status st = build_batch(*b, ms, n, false, bn1, bn2);
     if (st != QED_OK) {
         b->release();
         delete b;

@@ -51,6 +51,9 @@ void split_batch_destroy(Batch *b);
 // Times the grouped launches' tile widths on whole batched steps; keeps the fastest in the
 // models (used by the next split_batch_create of models that all carry it).
 qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, int steps, std::string &choice);
+// Sets the tile plan of the model's products (what the tuners choose) and rebuilds its step
+// tables; the grouped launches take the two widths.
+qed_status split_set_plan(qed_model *m, int bn1, int splits1, int bn2, int splits2, cudaStream_t s);
 void split_release(qed_model *m);
 
 }  // namespace qed

@@ -174,6 +174,30 @@ def test_batched_autotune_keeps_parity():
         qed.autotune_batched(m64)
 
 
+_WIDTH_REFS = {}
+
+
+@pytest.mark.parametrize("widths", [(256, 256), (128, 256), (128, 128)])
+def test_batched_tile_widths_keep_parity(widths):
+    """The grouped launches with each pair of tile widths (set on every model with
+    qed_set_plan): uneven chains with 128-column remainders and up to six jumps."""
+    specs = W.batched_chains(6, seed=13, dim_lo=60, dim_hi=660, n_steps=120, record_every=60)
+    if "refs" not in _WIDTH_REFS:
+        _WIDTH_REFS["refs"] = []
+        for m in specs:
+            b = oracle.enumerate_basis(m)
+            _WIDTH_REFS["refs"].append(oracle.evolve(m, n_steps=120, record_every=60, basis=b,
+                                                     obs_ids=list(range(b.dim))))
+    models, rhos = _setup(specs, "split_fp16x2")
+    for gm in models:
+        gm.set_plan(widths[0], 1, widths[1], 1)
+    recs = qed.evolve_batched(models, rhos, 120, record_every=60)
+    torch.cuda.synchronize()
+    for (rho_ref, rec_ref), gm, r, rec in zip(_WIDTH_REFS["refs"], models, rhos, recs):
+        assert np.abs(r.cpu().numpy() - rho_ref).max() <= 1e-5, (widths, gm.dim)
+        assert np.abs(rec.cpu().numpy() - rec_ref).max() <= 1e-6, (widths, gm.dim)
+
+
 def test_batched_argument_errors():
     specs = W.batched_chains(2, seed=1, dim_lo=32, dim_hi=64)
     models, rhos = _setup(specs, "split_fp16x2")

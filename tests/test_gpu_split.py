@@ -277,3 +277,96 @@ def test_autotuned_plan_keeps_parity(make, steps):
     gm.sync()
     assert np.abs(rho.cpu().numpy() - rho_ref).max() <= RHO_TOL
     assert np.abs(rec.cpu().numpy() - rec_ref).max() <= POP_TOL
+
+
+def test_split_runs_are_bitwise_repeatable():
+    """Every reduction of the split path has a fixed order (split-K slices summed in cluster
+    rank order, block reductions in shared memory, no atomics), so two runs from the same
+    state give the same bits: single models (the headline workload and a ragged dim-129
+    lattice), a batch of uneven chains, and the adjoint's loss and gradients."""
+    for m in (W.hb_shaped(), W.lattice(8, 8, seed=2)):
+        gm = qed.Model(m, precision="split_fp16x2")
+        rho0 = _cuda(W.random_density(gm.dim, seed=8, rank=4))
+        r1, r2 = rho0.clone(), rho0.clone()
+        gm.evolve(r1, 300)
+        gm.evolve(r2, 300)
+        gm.sync()
+        assert torch.equal(r1, r2), m["name"]
+    specs = W.batched_chains(6, seed=9, dim_lo=40, dim_hi=400, n_steps=100)
+    models = [qed.Model(s, precision="split_fp16x2") for s in specs]
+    runs = []
+    for _ in range(2):
+        rhos = [_cuda(W.random_density(gm.dim, seed=3, rank=2)) for gm in models]
+        qed.evolve_batched(models, rhos, 100)
+        runs.append(rhos)
+    torch.cuda.synchronize()
+    for a, b in zip(*runs):
+        assert torch.equal(a, b)
+    m = W.adjoint_lattice(6, 6, seed=1)
+    gm = qed.Model(m, precision="split_fp16x2")
+    rho0 = _cuda(oracle.initial_density(m, oracle.enumerate_basis(m)))
+    w = torch.zeros(gm.dim, dtype=torch.float64, device="cuda")
+    w[1] = 1.0
+    g1 = [x.clone() for x in gm.adjoint(rho0, 50, w, checkpoint_every=20)]
+    g2 = [x.clone() for x in gm.adjoint(rho0, 50, w, checkpoint_every=20)]
+    for a, b in zip(g1, g2):
+        assert torch.equal(a, b)
+
+
+_PLAN_REF = {}
+
+
+def _plan_ref(key, make, steps):
+    if key not in _PLAN_REF:
+        m = make()
+        b = oracle.enumerate_basis(m)
+        rho0 = W.random_density(b.dim, seed=12, rank=3)
+        rho_ref, rec_ref = oracle.evolve(m, rho0=rho0, n_steps=steps, record_every=steps // 2, basis=b,
+                                         obs_ids=list(range(b.dim)))
+        _PLAN_REF[key] = (m, rho0, rho_ref, rec_ref)
+    return _PLAN_REF[key]
+
+
+@pytest.mark.parametrize("plan", [(256, 1, 256, 1), (256, 2, 256, 2), (128, 4, 256, 4), (256, 1, 128, 1),
+                                  (128, 8, 128, 2), (256, 4, 256, 1)])
+@pytest.mark.parametrize("key,make,steps", [
+    ("lattice_d129", lambda: W.lattice(8, 8, seed=2), 150),
+    ("hb_d512", lambda: W.hb_shaped(), 100),
+    ("chain_d600", lambda: W.chain_instance(np.random.default_rng(4), 600, 600), 60),
+])
+def test_tile_plans_keep_parity(key, make, steps, plan):
+    """Every tile plan qed_set_plan accepts gives the oracle's step: 128- and 256-wide tiles
+    for both products (a 256-wide GEMM2 tile covers two 64-column groups, the second past D
+    at dim 129; the last 256-wide GEMM1 column tile at dims 129 and 600 has 128 columns),
+    1 to 8 K slices summed in the cluster, from a random mixed state (every element
+    nonzero)."""
+    m, rho0, rho_ref, rec_ref = _plan_ref(key, make, steps)
+    gm = qed.Model(m, precision="split_fp16x2")
+    kb = 2 * (-(-gm.dim // 128) * 128) // 64  # 64-wide K blocks of both products (K = 2 Dp)
+
+    def splits_fit(sp):
+        return -(-kb // -(-kb // sp)) == sp
+    if not (splits_fit(plan[1]) and splits_fit(plan[3])):
+        # e.g. 8 slices of 20 K blocks: the slices would not be equal powers of two
+        with pytest.raises(qed.QedError) as ei:
+            gm.set_plan(*plan)
+        assert ei.value.status == qed.QED_EINVAL
+        return
+    gm.set_plan(*plan)
+    rho = _cuda(rho0)
+    rec = gm.evolve(rho, steps, record_every=steps // 2, obs_ids=list(range(gm.dim)))
+    gm.sync()
+    assert np.abs(rho.cpu().numpy() - rho_ref).max() <= RHO_TOL, plan
+    assert np.abs(rec.cpu().numpy() - rec_ref).max() <= POP_TOL, plan
+
+
+def test_set_plan_rejects_bad_plans():
+    gm = qed.Model(W.jch_two_cavities(), precision="split_fp16x2")
+    for bad in [(64, 1, 128, 1), (128, 3, 128, 1), (128, 1, 128, 8), (128, 16, 128, 1), (256, 1, 512, 1)]:
+        with pytest.raises(qed.QedError) as ei:
+            gm.set_plan(*bad)
+        assert ei.value.status == qed.QED_EINVAL
+    g64 = qed.Model(W.jch_two_cavities(), precision="fp64")
+    with pytest.raises(qed.QedError) as ei:
+        g64.set_plan(128, 1, 128, 1)
+    assert ei.value.status == qed.QED_EUNSUPPORTED
