@@ -752,9 +752,15 @@ qed_status upload(T **dst, const std::vector<T> &v) {
 // The plans of a model's two products: GEMM1 [W_re; W_im] = A1 . rho^T (2Dp x Dp, K 2Dp, four
 // plane pairs), GEMM2 [X_re | X_im] = W . B2^T (Dp x 2Dp, K 2Dp, three plane pairs).  Widths and
 // splits = CTAs per cluster (on-chip reduction of the split-K slices) as given, or 0 for the
-// planner's rule (256-wide tiles once they fill half the SMs).
+// planner's rule (256-wide tiles once the tiles that run fill half the SMs).
 bool plan_products(SplitState &S, TcGemm &g1, TcGemm &g2, int splits1, int bn1, int splits2, int bn2 = 0) {
     const int Dp = (int)S.Dp;
+    if (bn2 == 0) {
+        // GEMM2 runs only the tiles on or above the diagonal: nm (nm + 1) / 2 of them when 256
+        // wide (nm = Dp / 128), which must fill half the SMs
+        const int nm = Dp / kTcBM;
+        bn2 = nm * (nm + 1) >= S.num_sms ? 256 : 128;
+    }
     return tc_gemm_plan(g1, S.a1, 3, S.rho_pl, 2, 2 * Dp, Dp, 2 * Dp, 4, kSeg1Pairs, S.num_sms, splits1, bn1, true) &&
            tc_gemm_plan(g2, S.w_pl, 2, S.b2, 3, Dp, 2 * Dp, 2 * Dp, 3, kSeg2Pairs, S.num_sms, splits2, bn2, true);
 }
