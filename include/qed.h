@@ -360,6 +360,18 @@ qed_status qed_profile(qed_model *m, void *rho, int64_t n_steps, double *ms, int
                        char *names, int32_t name_cap, qed_stream stream);
 
 /*
+ * The kernels of a split-precision model's Lie step timed one at a time in steady state:
+ * imports rho (not modified), runs one step, then replays each kernel (GEMM1, GEMM2, the
+ * Lindblad update) `reps` times back to back from a CUDA graph, as the step loop runs
+ * them (each launch's set-up overlapping the previous one's tail), and writes the mean
+ * milliseconds per launch into ms[0..n_kernels-1] and the names (comma separated) into
+ * names (size name_cap).  Each kernel repeats identical work: it reads only what the
+ * others write.  Synchronises.  EUNSUPPORTED for FP64 models and the other schemes.
+ */
+qed_status qed_profile_replay(qed_model *m, void *rho, int32_t reps, double *ms, int32_t n_kernels, char *names,
+                              int32_t name_cap, qed_stream stream);
+
+/*
  * The tensor-core product of the split-precision step, exposed for testing:
  *     out[s] = sum over the K-slices of slice s of  sum_q A_{pa(q)} B_{pb(q)}^T
  * with A = a_planes (device FP16 [planes_a][M][K], K contiguous), B = b_planes (device

@@ -89,6 +89,7 @@ def lib():
         "qed_get_U": [vp, vp, vp],
         "qed_profile": [vp, vp, i64, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_launch_count": [ctypes.POINTER(i64)],
+        "qed_profile_replay": [vp, vp, i32, _c_double_p, i32, ctypes.c_char_p, i32, vp],
         "qed_adjoint": [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "qed_evolve_batched": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, i32, ctypes.POINTER(vp), vp],
         "qed_select_states": [vp, vp, i64, i32, dbl, ctypes.POINTER(vp), vp, ctypes.POINTER(i64),
@@ -457,6 +458,22 @@ class Model:
                "qed_profile")
         labels = [x for x in names.value.decode().split(",") if x]
         return dict(zip(labels, ms[: len(labels)].tolist()))
+
+    def profile_replay(self, rho, reps=200, stream=None):
+        """Mean milliseconds per launch of each kernel of the split Lie step, every kernel
+        replayed back to back from a CUDA graph (qed_profile_replay)."""
+        return _profile_replay(self, rho, reps, stream)
+
+
+def _profile_replay(model, rho, reps, stream=None):
+    _check_rho(rho, model.dim)
+    ms = np.zeros(8, dtype=np.float64)
+    names = ctypes.create_string_buffer(512)
+    _check(lib().qed_profile_replay(model._h, ctypes.c_void_p(rho.data_ptr()), int(reps),
+                                    ms.ctypes.data_as(_c_double_p), 8, names, 512, _stream_handle(stream)),
+           "qed_profile_replay")
+    labels = [x for x in names.value.decode().split(",") if x]
+    return dict(zip(labels, ms[: len(labels)].tolist()))
 
 
 def evolve_batched(models, rhos, n_steps, record_every=0, records=None, stream=None):

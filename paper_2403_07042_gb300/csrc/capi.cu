@@ -890,6 +890,27 @@ qed_status qed_select_states(qed_model *m, const void *rho0, int64_t steps_per_r
     return QED_OK;
 }
 
+qed_status qed_profile_replay(qed_model *m, void *rho_v, int32_t reps, double *ms, int32_t n_kernels, char *names,
+                              int32_t name_cap, qed_stream stream) {
+    if (!m || !rho_v || !ms || reps <= 0) return einval("bad argument");
+    if (m->prec == QED_FP64) {
+        set_error("qed_profile_replay: split-precision models only");
+        return QED_EUNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    QED_TRY(split_begin(m, (const double2 *)rho_v, s));
+    std::vector<double> acc;
+    std::string label;
+    QED_TRY(split_profile_replay(m, s, reps, acc, label));
+    for (int c = 0; c < n_kernels; ++c) ms[c] = c < (int)acc.size() ? acc[(size_t)c] : 0.0;
+    if (names && name_cap > 0) {
+        std::strncpy(names, label.c_str(), (size_t)name_cap - 1);
+        names[name_cap - 1] = 0;
+    }
+    QED_CUDA_TRY(cudaStreamSynchronize(s));
+    return QED_OK;
+}
+
 qed_status qed_profile(qed_model *m, void *rho_v, int64_t n_steps, double *ms, int32_t n_kernels, char *names,
                        int32_t name_cap, qed_stream stream) {
     if (!m || !rho_v || !ms || n_steps <= 0) return einval("bad argument");

@@ -1291,6 +1291,59 @@ void split_set_scheme(qed_model *m, int scheme) {
     if (m->sp) m->sp->self.scheme = scheme;
 }
 
+// Each kernel of the Lie step replayed `reps` times back to back from a CUDA graph (the way
+// the step loop runs them: programmatic dependent launch overlapping one launch's set-up
+// with the previous one's tail), after one full step so that W, V and the planes hold
+// this state's values.  Each kernel only reads what the others write and overwrites its
+// own outputs with the same values, so the replay repeats identical work.  ms[c] = mean
+// milliseconds per launch.
+qed_status split_profile_replay(qed_model *m, cudaStream_t s, int reps, std::vector<double> &ms, std::string &label) {
+    const Batch &b = m->sp->self;
+    if (b.scheme != QED_SCHEME_LIE) {
+        set_error("qed_profile_replay: the Lie step only");
+        return QED_EUNSUPPORTED;
+    }
+    batch_step(b, m->err, s);
+    cudaStream_t cap = nullptr;
+    QED_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    qed_status st = QED_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = QED_ECUDA;
+    ms.assign(3, 0.0);
+    for (int c = 0; c < 3 && st == QED_OK; ++c) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            st = QED_ECUDA;
+            break;
+        }
+        const int64_t before = launches();
+        for (int r = 0; r < reps; ++r) {
+            if (c == 0) launch_gemm1(b, m->err, cap);
+            else if (c == 1) launch_gemm2(b, m->err, cap);
+            else launch_dissipate(b, cap);
+        }
+        count_launches(-(launches() - before));
+        const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = QED_ECUDA;
+        if (graph) cudaGraphDestroy(graph);
+        float t = 0.f;
+        if (st == QED_OK && (cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+                             cudaGraphLaunch(exec, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+            st = QED_ECUDA;
+        count_launches(2 * (int64_t)reps);
+        ms[(size_t)c] = (double)t / reps;
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+    if (st == QED_ECUDA) set_error(std::string("qed_profile_replay: ") + cudaGetErrorString(cudaGetLastError()));
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(cap);
+    label = "gemm1_tc,gemm2_tc_v,dissipate";
+    return st;
+}
+
 int split_step_timed(qed_model *m, cudaStream_t s, std::string &label) {
     const Batch &b = m->sp->self;
     if (b.scheme == QED_SCHEME_STRANG) {

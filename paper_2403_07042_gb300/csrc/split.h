@@ -54,6 +54,8 @@ qed_status split_autotune_batched(qed_model *const *ms, int n, cudaStream_t s, i
 // Sets the tile plan of the model's products (what the tuners choose) and rebuilds its step
 // tables; the grouped launches take the two widths.
 qed_status split_set_plan(qed_model *m, int bn1, int splits1, int bn2, int splits2, cudaStream_t s);
+// Per-kernel durations of the Lie step with each kernel replayed back to back from a graph.
+qed_status split_profile_replay(qed_model *m, cudaStream_t s, int reps, std::vector<double> &ms, std::string &label);
 void split_release(qed_model *m);
 
 }  // namespace qed

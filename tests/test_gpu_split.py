@@ -370,3 +370,24 @@ def test_set_plan_rejects_bad_plans():
     with pytest.raises(qed.QedError) as ei:
         g64.set_plan(128, 1, 128, 1)
     assert ei.value.status == qed.QED_EUNSUPPORTED
+
+
+def test_profile_replay():
+    """qed_profile_replay times each kernel of the Lie step replayed back to back; it leaves
+    the caller's rho untouched and the model's next evolution matches the oracle."""
+    m = W.jch_two_cavities()
+    b = oracle.enumerate_basis(m)
+    gm = qed.Model(m, precision="split_fp16x2")
+    rho = _cuda(oracle.initial_density(m, b))
+    before = rho.clone()
+    kern = gm.profile_replay(rho, 20)
+    assert list(kern) == ["gemm1_tc", "gemm2_tc_v", "dissipate"] and all(v > 0 for v in kern.values())
+    assert torch.equal(rho, before)
+    rho_ref = oracle.evolve(m, n_steps=100, basis=b, return_records=False)
+    gm.evolve(rho, 100)
+    gm.sync()
+    assert np.abs(rho.cpu().numpy() - rho_ref).max() <= RHO_TOL
+    g64 = qed.Model(m, precision="fp64")
+    with pytest.raises(qed.QedError) as ei:
+        g64.profile_replay(before, 5)
+    assert ei.value.status == qed.QED_EUNSUPPORTED
