@@ -2,16 +2,21 @@
 // "unitary evolution" stage (Sec. 4.2, Table 3) in split precision.
 //
 // One CTA computes one output tile (128 x BN, BN = 128 or 256) of one split-K slice:
-//   warp 0, one lane : TMA producer, ring of (A 128x64, B BNx64) FP16 tiles of the current
-//                      segment's planes, 128-byte swizzled, completion tracked by mbarrier
-//                      transaction bytes; the first stages of the constant operand are
-//                      requested before the wait on the previous kernel of the step
-//   warp 1, one lane : MMA issuer, tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16)
-//                      into a TMEM accumulator; tcgen05.commit frees each smem stage
-//   epilogue         : kEpiPlain (4 warps) stores the slice; kEpiW / kEpiV (8 warps) copy the
-//                      accumulator into shared memory, sum the cluster's split-K slices
+//   warp 0, one lane : TMA producer, ring of FP16 tiles (A 128x64, B BNx64), 128-byte
+//                      swizzled, completion tracked by mbarrier transaction bytes.  The
+//                      plain product walks the segments' K blocks one plane pair per stage;
+//                      the step's products (kEpiW, kEpiV) load every plane of both operands
+//                      for one 64-wide K block into one stage (2 stages)
+//   warp 1, one lane : MMA issuer, tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16);
+//                      the step's products issue every plane product of the stage, the
+//                      leading one (hi x hi) into one TMEM accumulator and the corrections
+//                      into a second; tcgen05.commit frees each smem stage
+//   epilogue         : kEpiPlain (4 warps) stores the slice; kEpiW / kEpiV (8 warps) add the
+//                      two accumulators into shared memory, sum the cluster's split-K slices
 //                      through distributed shared memory and write W (and its FP16 planes)
 //                      or V = U rho U^+ (gemm_tc.h)
+// All set-up (barriers, TMEM allocation, tensor-map prefetch) comes before the wait on the
+// previous kernel of the step (programmatic dependent launch); every load comes after it.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel records
 // kErrTimeout, stops issuing work, waits (bounded) for what it issued, frees TMEM and
 // returns.  Every CTA of a cluster reaches each cluster barrier exactly once on every path.
