@@ -489,22 +489,38 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
         }
         return;
     }
-    pdl_wait();
-    pdl_trigger();
-    // incoming lists: the rows one after another; lanes outside the matrix stay to the end of
-    // every row (with clamped indices, no stores), since the warp shares the merge of long
-    // jump lists
-#pragma unroll 1
+    // incoming lists: the damping rates and list bounds of the thread's rows (static
+    // tables) before the dependency wait, the rows' V elements together after it, then the
+    // rows' merges one after another; lanes outside the matrix stay to the end of every row
+    // (with clamped indices, no stores), since the warp shares the merge of long jump lists
+    float2 dmr[kRows];
+    int pr[kRows], per[kRows];
+    const int q0 = n_in ? a.in_ptr[n] : 0, qe0 = n_in ? a.in_ptr[n + 1] : 0;
+#pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const int64_t m = m0 + 8 * r;
         const bool inside = m < D && n_in;
-        const int64_t mc = inside ? m : 0;
-        const float2 dm = a.damp[m < D ? m : 0];
-        const cdf v = load_cdf(X[mc * D + nc]);
+        dmr[r] = a.damp[m < D ? m : 0];
+        pr[r] = inside ? a.in_ptr[m] : 0;
+        per[r] = inside ? a.in_ptr[m + 1] : 0;
+    }
+    pdl_wait();
+    pdl_trigger();
+    float4 vr[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int64_t m = m0 + 8 * r;
+        vr[r] = X[(m < D && n_in ? m : 0) * D + nc];
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const int64_t m = m0 + 8 * r;
+        const bool inside = m < D && n_in;
+        const cdf v = load_cdf(vr[r]);
         float gr, gi;
-        damping_term(dm, dn, v, gr, gi);
-        int p = inside ? a.in_ptr[m] : 0, pe = inside ? a.in_ptr[m + 1] : 0;
-        int q = inside ? a.in_ptr[n] : 0, qe = inside ? a.in_ptr[n + 1] : 0;
+        damping_term(dmr[r], dn, v, gr, gi);
+        int p = pr[r], pe = per[r];
+        int q = inside ? q0 : 0, qe = inside ? qe0 : 0;
         // long lists: merged by the whole warp
         const bool is_long = long_merge_df(a.err, D, a.in_jump, a.in_src, a.coef, X, p, pe, q, qe, gr, gi);
         if (is_long) pe = p;  // done: skip the serial merge
