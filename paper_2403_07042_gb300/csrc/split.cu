@@ -392,12 +392,14 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
         for (int j = 0; j < kInMax; ++j) tn[j] = j < nj ? a.jtab[nc * kInMax + j] : make_int4(-1, 0, 0, 0);
         pdl_wait();
         pdl_trigger();
-        float4 v[kRows], u[kRows][kInMax];
+        float4 v[kRows], u[kRows][kInMax], bv[kRows];
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             const int64_t m = m0 + 8 * r;
             const bool inside = m < D && n_in;
             v[r] = X[(inside ? m : 0) * D + nc];
+            // the base of a Strang stage comes with the gathers
+            if (!LIE) bv[r] = B ? B[(inside ? m : 0) * D + nc] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < kInMax; ++j) {
                 const bool hit = inside && tm[r][j].x >= 0 && tn[j].x >= 0 &&
@@ -421,7 +423,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
                 gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
                 gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
             }
-            const cdf b = LIE ? vv : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
+            const cdf b = LIE ? vv : load_cdf(bv[r]);
             lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
         }
         return;
@@ -443,13 +445,14 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
         pdl_wait();
         pdl_trigger();
         // every load of the kRows elements issued before the first use
-        float4 v[kRows], u[kRows][kInMax];
+        float4 v[kRows], u[kRows][kInMax], bv[kRows];
         float2 cq[kRows][kInMax];
         bool hit[kRows][kInMax];
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             const int64_t m = m0 + 8 * r;
             const bool inside = m < D && n_in;
+            if (!LIE) bv[r] = B ? B[(inside ? m : 0) * D + nc] : make_float4(0.f, 0.f, 0.f, 0.f);
             v[r] = X[(inside ? m : 0) * D + nc];
 #pragma unroll
             for (int i = 0; i < kInMax; ++i) {
@@ -484,7 +487,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
                 gr = __fmaf_rn(c.hi, ur, __fmaf_rn(c.lo, ur, gr));
                 gi = __fmaf_rn(c.hi, ui, __fmaf_rn(c.lo, ui, gi));
             }
-            const cdf b = LIE ? vv : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
+            const cdf b = LIE ? vv : load_cdf(bv[r]);
             lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
         }
         return;
@@ -506,11 +509,12 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
     }
     pdl_wait();
     pdl_trigger();
-    float4 vr[kRows];
+    float4 vr[kRows], bv[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const int64_t m = m0 + 8 * r;
         vr[r] = X[(m < D && n_in ? m : 0) * D + nc];
+        if (!LIE) bv[r] = B ? B[(m < D && n_in ? m : 0) * D + nc] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -542,7 +546,7 @@ __device__ __forceinline__ void lindblad_update(const TileItem *__restrict__ til
             }
         }
         if (!inside) continue;
-        const cdf b = LIE ? v : (B ? load_cdf(B[m * D + n]) : cdf{{0.f, 0.f}, {0.f, 0.f}});
+        const cdf b = LIE ? v : load_cdf(bv[r]);
         lindblad_store<LIE>(a, O, m, n, b, f, gr, gi, planes);
     }
 }
