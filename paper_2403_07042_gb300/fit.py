@@ -24,7 +24,7 @@ def fit_final_populations(model, target, n_steps, names=("g",), precision="fp64"
     target a length-D array.  Returns (fitted model dictionary, list of F per iteration)."""
     import torch
     m = dict(model)
-    tgt = torch.as_tensor(np.asarray(target, dtype=np.float64), device="cuda")
+    tgt = torch.tensor(np.asarray(target, dtype=np.float64), device="cuda")  # a copy: target may be read-only
     k = checkpoint_every or n_steps
 
     def run(mm):
